@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Throughput benchmark: particle-steps/s of the 3,000,000-particle DPD fluid
+(periodic cube L = 100, rho = 3, a = 25, gamma = 4.5, kT = 1, s = 1,
+dt = 0.01) on one GB300, through the C ABI of libdpd.so.
+
+A step is one full pass of the hot path: velocity-Verlet phase 1 with the
+per-particle signature and displacement check, the cell/reorder/neighbour
+chain (runs on the steps where a particle has moved more than skin/2), the
+fused pair force, and phase 2.  The timed region is K steps replayed from
+CUDA graphs, timed with CUDA events on the library's stream; the working
+set (positions, velocities, forces, reference positions and the neighbour
+table, ~0.9 GB) is larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own independent box (no data
+exchange: replicas), timing is the max over ranks after a barrier, and the
+value is the aggregate particle-steps/s.  ``--impl reference`` times the FP64
+CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle-steps/s (3M-particle DPD fluid, 1 GB300)"
+UNIT = "particle-steps/s"
+WORKLOAD = "fluid_large"
+# ALU peak from unit counts and clock: 152 SMs x 128 FP32/INT32 lanes x 2.07 GHz
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# algorithmic lane-ops per unique interacting pair (distance, weights,
+# TEA-4 pair hash, Box-Muller, force, accumulation on both particles)
+OPS_PER_PAIR = 100.0
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+        self.windows = []
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark(self):
+        return time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 10:
+                        continue
+                    try:
+                        ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                        frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                        rows.append((ts + frac, float(parts[2]), float(parts[3]), parts[6:10], parts[5]))
+                    except Exception:
+                        continue
+        except Exception:
+            pass
+        sel = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15] or rows[-5:]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in sel for k in range(4) if r[3][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max(r[2] for r in sel),
+                "reasons": reasons, "samples": len(sel)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_traffic():
+    """DRAM bytes per force-kernel launch from the committed ncu summary, if
+    it was taken on the current kernel source (else None)."""
+    path = os.path.join(PROFILES, "force_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_1311_0402_gb300", "csrc", "kernels_force.cu"), "rb").read()
+        if rec.get("kernels_force_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+def oracle_rate(x, v, cfg, nsteps, box):
+    """Particle-steps/s of the FP64 oracle (single-threaded C) on a state."""
+    import oracle
+    sysm = oracle.System(box, cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"], lam=cfg["lam"])
+    f0, _ = sysm.forces(x, v, step=0)
+    t0 = time.perf_counter()
+    sysm.run(x, v, nsteps, f=f0)
+    dt = time.perf_counter() - t0
+    return x.shape[0] * nsteps / dt, dt
+
+
+def run_reference(args):
+    """The oracle as the reference arm: FP64 CPU, host cores, on a bounded
+    sample of the workload (a 30^3 sub-box of the same fluid) per step."""
+    import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg = workloads.CONFIGS[args.workload]
+    sub = (30.0, 30.0, 30.0)
+    st = workloads.make(args.workload, box=sub)
+    import oracle
+    sysm = oracle.System(sub, cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"], lam=cfg["lam"])
+    f, _ = sysm.forces(st["x"], st["v"], step=0)
+    res = sysm.run(st["x"], st["v"], args.warmup, f=f)
+    t0 = time.perf_counter()
+    res = sysm.run(res["x"], res["v"], args.steps, f=res["f"], step=res["step"])
+    el = time.perf_counter() - t0
+    value = st["n"] * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s: periodic L=100 rho=3 DPD fluid (3,000,000 particles), a=25 gamma=4.5 kT=1 "
+                               "s=1 dt=0.01" % args.workload, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "FP64 oracle (single-threaded C), each step on a 30^3 sub-box of the same "
+                                   "fluid (%d particles, rho=3)" % st["n"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = tdist
+    import paper_1311_0402_gb300 as dpd
+    if rank == 0:
+        dpd.build()
+    if pg:
+        pg.barrier()
+    dpd.lib()
+    import workloads
+
+    cfg = workloads.CONFIGS[args.workload]
+    st = workloads.make(args.workload, seed=workloads.BASE_SEED + cfg["seed_offset"] + 1000 * rank)
+    n = st["n"]
+    stream = torch.cuda.Stream()
+    sim = dpd.Sim(cfg["box"], cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"], lam=cfg["lam"],
+                  skin=0.3, seed=workloads.TEA_SEED, stream=stream.cuda_stream)
+    sim.set_state(st["x"], st["v"])
+    sim.step(args.warmup)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    # ---------------------------------------------------------- timed region
+    chunk = 1000
+    chunks = [chunk] * (args.steps // chunk) + ([args.steps % chunk] if args.steps % chunk else [])
+    for c in sorted(set(chunks)):  # capture the graphs outside the timed region
+        sim.step_profiled(c)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    times = []
+    for c in chunks:
+        times.append(sim.step_profiled(c))
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if pg:
+        pg.barrier()
+    # ------------------------------------------------------------------------
+    time.sleep(0.25)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    total_ms = sum(t["total_ms"] for t in times)
+    force_ms = sum(t["force_ms"] for t in times)
+    force_launches = sum(t["force_launches"] for t in times)
+    launches = sum(t["kernel_launches"] for t in times)
+    rebuilds = sum(t["rebuilds"] for t in times)
+    integ_ms = sum(t["integrate_ms"] for t in times)
+    rebuild_ms = sum(t["rebuild_ms"] for t in times)
+    max_ms = total_ms
+    if pg:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        max_ms = float(tt.item())
+    value = ws * n * args.steps / (max_ms / 1e3)
+
+    # roofline of the dominant kernel (the fused pair force)
+    rho = n / float(np.prod(cfg["box"]))
+    pairs_per_particle = 0.5 * rho * 4.0 / 3.0 * np.pi * cfg["rc"] ** 3
+    ops_per_launch = n * pairs_per_particle * OPS_PER_PAIR
+    force_avg_s = force_ms / 1e3 / max(force_launches, 1)
+    achieved = ops_per_launch / force_avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "TOP/s",
+                "frac": achieved / ALU_PEAK_TOPS, "traffic": kernel_traffic(),
+                "kernel": "k_force", "avg_launch_ms": force_avg_s * 1e3,
+                "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and max clock)"}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (152 * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    # end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    x_host = np.ascontiguousarray(st["x"])
+    v_host = np.ascontiguousarray(st["v"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.set_state(x_host, v_host)
+    for _ in range(e2e_steps):
+        sim.step(1)
+        sim.observables()
+    xo, vo, _ = sim.state()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    state_bytes = n * 6 * 8
+    obs_bytes = 8 * 8 * ((n + 255) // 256) + 64  # per-block partials + control word
+    e2e = {"value": ws * n * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(state_bytes / e2e_steps),
+           "d2h_bytes_per_step": int(state_bytes / e2e_steps + obs_bytes),
+           "steps": e2e_steps,
+           "what": "dpd_set_state from host arrays, then per step dpd_step(1) + dpd_observables, then "
+                   "dpd_get_state to host arrays"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "%s: periodic L=100 rho=3 DPD fluid (%d particles per GPU), a=25 gamma=4.5 kT=1 "
+                               "s=1 dt=0.01 lambda=0.5, skin 0.3, displacement-triggered rebuilds" % (args.workload, n),
+                   "parallelism": "replicas" if ws > 1 else "single", "l2": "working set > L2 (no flush)"},
+        "phases_ms": {"integrate": integ_ms, "rebuild": rebuild_ms, "force": force_ms, "rebuilds": rebuilds},
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample_steps = 2
+        rate, secs = oracle_rate(xo, vo, cfg, sample_steps, cfg["box"])
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "FP64 oracle (single-threaded C), %d steps of the full %d-particle box "
+                                          "(%.1f s)" % (sample_steps, n, secs)}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * dpd.h -- C ABI of the GB300 DPD pair-interaction engine (libdpd.so).
+ *
+ * The engine advances a periodic system of dissipative-particle-dynamics
+ * (DPD) particles on one GPU: cell binning and reordering, a cutoff
+ * neighbour list, the fused conservative + dissipative + random pair force
+ * with a pair-symmetric counter-based Gaussian, harmonic bonds, a body force
+ * and the lambda form of velocity Verlet.  Method: Tang & Karniadakis,
+ * "Accelerating Dissipative Particle Dynamics Simulations on GPUs"
+ * (arXiv:1311.0402); each entry point cites the passage that defines what it
+ * computes.
+ *
+ * Conventions for every entry point:
+ *   - Host arrays are owned by the caller; the library copies what it needs
+ *     before returning and keeps no pointer to them.
+ *   - The library owns all device memory of a handle (allocated by
+ *     dpd_create / dpd_set_state, freed by dpd_destroy).
+ *   - Calls are synchronous: results are complete when the call returns.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Particle arrays passed in are in the caller's order ("particle index"
+ *     0..n-1); every array passed out uses that same order, whatever
+ *     reordering the engine does internally.
+ *   - Vectors are n x 3 row-major doubles (x0 y0 z0 x1 y1 z1 ...).
+ *   - Status codes: DPD_OK on success.  DPD_ERR_ARG for invalid arguments
+ *     (the handle's state is left unchanged).  A CUDA failure latches
+ *     DPD_ERR_CUDA on the handle.  dpd_last_error() describes the last
+ *     failure.
+ */
+#ifndef DPD_H
+#define DPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dpd_sim dpd_sim; /* opaque handle */
+
+typedef enum {
+    DPD_OK = 0,
+    DPD_ERR_ARG = 1,          /* invalid argument; nothing changed */
+    DPD_ERR_OOM = 2,          /* device or host allocation failed */
+    DPD_ERR_CUDA = 3,         /* a CUDA call failed (latched) */
+    DPD_ERR_NBR_OVERFLOW = 4, /* a particle had more neighbours than the list holds */
+    DPD_ERR_NONFINITE = 5,    /* a force or position became NaN / Inf */
+    DPD_ERR_TIMEOUT = 6,      /* the GPU did not finish within the wait limit */
+    DPD_ERR_STATE = 7         /* call order: e.g. dpd_step before dpd_set_state */
+} dpd_status;
+
+/* Run options.  Fill with dpd_default_options() and override fields. */
+typedef struct {
+    double skin;              /* neighbour-list skin added to r_c (default 0.3) */
+    int32_t rebuild_every;    /* 0 (default): rebuild when a particle has moved more
+                                 than skin/2 since the last build; k > 0: also
+                                 rebuild at least every k steps */
+    int32_t body_force_mode;  /* 0 none, 1 uniform g, 2 +g for y < L_y/2 and -g above
+                                 (reverse Poiseuille, Sec. 4.2 of the paper) */
+    uint64_t seed;            /* global seed of the random force (default 42) */
+    double lambda;            /* velocity-Verlet prediction factor (default 0.5) */
+    double body_force[3];     /* g (force per particle, unit mass) */
+    int32_t nbr_capacity;     /* neighbours per particle; 0 = from density */
+    int32_t graph_steps;      /* steps per captured CUDA graph (default 8; 0 = no graphs) */
+    double wait_timeout_s;    /* host wait limit per call (default 600 s) */
+    void *stream;             /* cudaStream_t to run on; NULL = a stream of the handle */
+} dpd_options;
+
+/* Observables of the current full-step state (Alg. 1 "calculate statistics"). */
+typedef struct {
+    uint64_t step;
+    int64_t n;
+    double kinetic;      /* sum m v^2 / 2 (m = 1) */
+    double temperature;  /* sum m v^2 / (3N - 3) */
+    double virial;       /* sum_{i<j} r_ij . (F^C_ij + F^bond_ij) at the current positions */
+    double pressure;     /* (sum m v^2 + virial) / (3V) */
+    double momentum[3];  /* sum m v */
+} dpd_obs;
+
+/* Default options (skin 0.3, displacement-triggered rebuild, seed 42,
+ * lambda 0.5, no body force, automatic capacity, 8-step graphs). */
+void dpd_default_options(dpd_options *opt);
+
+/* Create a simulation handle.
+ * Defines the pair force of Eqs. 2-9 (Sec. 2): for |r_ij| < rc,
+ *   F_ij = [a_{t_i t_j} w - gamma w^{2s} (e_ij . v_ij) + sigma w^s xi_ij dt^{-1/2}] e_ij,
+ *   w = 1 - |r_ij| / rc, sigma = sqrt(2 gamma kT) (Eq. 9), r_ij = r_i - r_j.
+ * box:       three box lengths (periodic in all directions), each > 2 (rc + skin).
+ * n_species: 1..8; a_ij: n_species x n_species row-major, symmetric.
+ * gamma >= 0, kT >= 0, rc > 0, s > 0, dt > 0.  opt may be NULL (defaults).
+ * Returns DPD_ERR_ARG (and *out = NULL) on invalid parameters. */
+dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, const double *a_ij,
+                      double gamma, double kT, double rc, double s, double dt,
+                      const dpd_options *opt);
+
+/* Load particles (Alg. 1 "CPU -> GPU").  x, v: n x 3; positions are wrapped
+ * into [0, L) and rounded to FP32 on the device.  species: n entries in
+ * [0, n_species) or NULL (all 0).  tag: n distinct identity tags keying the
+ * random force, or NULL (tag = particle index).  step: the step number of
+ * this state (keys the random force).  Builds the cell and neighbour lists
+ * and computes the force at this state.  Replaces any previous state and
+ * drops previously set bonds. */
+dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v,
+                         const int32_t *species, const uint32_t *tag, uint64_t step);
+
+/* Harmonic bonds F = -K (r - r0) e_ij between particle indices (Sec. 4.5).
+ * pairs: nb x 2 particle indices (the order of dpd_set_state); each particle
+ * may appear in at most 6 bonds.  Bonded pairs also feel the pair force.
+ * Recomputes the force of the current state.  nb = 0 removes all bonds. */
+dpd_status dpd_set_bonds(dpd_sim *h, int64_t nb, const uint32_t *pairs, double k, double r0);
+
+/* Rebuild the cell list, particle order and neighbour list now (Secs. 3.2-3.3).
+ * The list holds every pair with d^2 < (rc + skin)^2 under the FP32
+ * minimum-image predicate d = x_j - x_i (per axis: d -= L if d > L/2, d += L
+ * if d < -L/2), d^2 = (dx dx + dy dy) + dz dz, each operation rounded. */
+dpd_status dpd_build_neighbors(dpd_sim *h);
+
+/* Copy the neighbour pairs of the current list as particle indices
+ * (i < j), at most cap pairs into pairs_out (cap x 2), and the number of
+ * distinct pairs into *n_out (which may exceed cap).  pairs_out may be
+ * NULL with cap = 0 to query the count. */
+dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64_t *n_out);
+
+/* Total force f_i = sum_j F_ij (Eq. 2) + bonds + body force at the current
+ * positions, velocities and step key, into f_out (n x 3, nullable).  Does
+ * not change the state.  Uses the current neighbour list, which every call
+ * leaves valid for the current positions (no particle has moved more than
+ * skin/2 since it was built). */
+dpd_status dpd_forces(dpd_sim *h, double *f_out);
+
+/* The force the integrator holds for the next step (n x 3). */
+dpd_status dpd_get_force(dpd_sim *h, double *f_out);
+
+/* Advance nsteps steps (Alg. 1 main loop, Sec. 3.1): for each step
+ *   x += dt v + dt^2/2 f;  v~ = v + lambda dt f;  rebuild lists if needed;
+ *   f' = F(x, v~, step + 1);  v += dt/2 (f + f');  step += 1.
+ * Returns DPD_ERR_NBR_OVERFLOW or DPD_ERR_NONFINITE if detected (the state
+ * is then unreliable; reload it with dpd_set_state). */
+dpd_status dpd_step(dpd_sim *h, int64_t nsteps);
+
+/* Per-phase device times of a run, measured with CUDA events recorded on
+ * the handle's stream around every kernel group of every step. */
+typedef struct {
+    double total_ms;        /* first to last event */
+    double integrate_ms;    /* velocity-Verlet phases (+ signature, displacement check) */
+    double rebuild_ms;      /* binning / scan / reorder / neighbour-list chain */
+    double force_ms;        /* fused pair force (+ bonds, body force) */
+    int64_t steps;
+    int64_t force_launches;
+    int64_t kernel_launches;
+    int64_t rebuilds;       /* rebuilds that ran during the call */
+} dpd_step_times;
+
+/* dpd_step with CUDA events around each kernel group of each step (the
+ * kernels and their order are those of dpd_step; the run is captured as a
+ * single CUDA graph of nsteps steps when graph_steps > 0).  times may be
+ * NULL. */
+dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *times);
+
+/* Observables of the current state. */
+dpd_status dpd_observables(dpd_sim *h, dpd_obs *out);
+
+/* Binned profile of v[vel_axis] along bin_axis (nbins equal bins over the
+ * box): sum_out[b] += sum of v, count_out[b] += number of particles.
+ * Both arrays have nbins entries and are accumulated into, not cleared. */
+dpd_status dpd_profile(dpd_sim *h, int32_t bin_axis, int32_t vel_axis, int32_t nbins,
+                       double *sum_out, double *count_out);
+
+/* Current state in the caller's particle order: x, v (n x 3, nullable) as
+ * stored on the device (FP32 values, wrapped into [0, L)), and the step. */
+dpd_status dpd_get_state(dpd_sim *h, double *x, double *v, uint64_t *step);
+
+/* Number of particles and of neighbour-list rebuilds so far. */
+dpd_status dpd_info(dpd_sim *h, int64_t *n, int64_t *rebuilds, int32_t *nbr_capacity);
+
+/* The pair random numbers, computed by the device kernels (Sec. 3.5):
+ * for each k, sig = TEA-16 signature of (bitrev(tag), step) under the key
+ * of seed, (A, B) = TEA-4 of (min(sig_i, sig_j), max(sig_i, sig_j)),
+ * out_hash[2k] = A, out_hash[2k+1] = B, out_xi[k] = the FP32 Gaussian
+ * sign(B) sqrt(-2 ln u1) cos(pi u2).  Host arrays of m (tags) and 2m / m
+ * entries; out_xi may be NULL.  Uses the current device; creates a
+ * temporary stream. */
+dpd_status dpd_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *tag_i,
+                        const uint32_t *tag_j, uint32_t *out_hash, float *out_xi);
+
+/* Description of the last failure on h (or of the last handle-less failure
+ * when h is NULL).  Valid until the next call on h. */
+const char *dpd_last_error(const dpd_sim *h);
+
+/* Free the handle and all its device memory.  NULL is ignored. */
+void dpd_destroy(dpd_sim *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPD_H */

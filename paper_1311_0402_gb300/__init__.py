@@ -1,0 +1,310 @@
+"""Python binding of libdpd.so, the GB300 DPD pair-interaction engine.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+behind the C ABI declared in ``include/dpd.h``.  The functions here carry the
+same names as the C entry points; ``Sim`` wraps a handle for convenience.
+There is no CPU fallback: importing works without a GPU, but every call
+that needs the library raises if ``libdpd.so`` is missing or no GPU is
+present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdpd.so")
+
+DPD_OK = 0
+STATUS = {0: "DPD_OK", 1: "DPD_ERR_ARG", 2: "DPD_ERR_OOM", 3: "DPD_ERR_CUDA", 4: "DPD_ERR_NBR_OVERFLOW",
+          5: "DPD_ERR_NONFINITE", 6: "DPD_ERR_TIMEOUT", 7: "DPD_ERR_STATE"}
+
+# every exported symbol declared in include/dpd.h
+EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds", "dpd_build_neighbors",
+           "dpd_get_neighbors", "dpd_forces", "dpd_get_force", "dpd_step", "dpd_observables", "dpd_profile",
+           "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled")
+
+
+class DPDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class dpd_options(ctypes.Structure):
+    _fields_ = [
+        ("skin", ctypes.c_double),
+        ("rebuild_every", ctypes.c_int32),
+        ("body_force_mode", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("lam", ctypes.c_double),
+        ("body_force", ctypes.c_double * 3),
+        ("nbr_capacity", ctypes.c_int32),
+        ("graph_steps", ctypes.c_int32),
+        ("wait_timeout_s", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class dpd_obs(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_uint64),
+        ("n", ctypes.c_int64),
+        ("kinetic", ctypes.c_double),
+        ("temperature", ctypes.c_double),
+        ("virial", ctypes.c_double),
+        ("pressure", ctypes.c_double),
+        ("momentum", ctypes.c_double * 3),
+    ]
+
+
+class dpd_step_times(ctypes.Structure):
+    _fields_ = [
+        ("total_ms", ctypes.c_double),
+        ("integrate_ms", ctypes.c_double),
+        ("rebuild_ms", ctypes.c_double),
+        ("force_ms", ctypes.c_double),
+        ("steps", ctypes.c_int64),
+        ("force_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("rebuilds", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force, verbose=verbose)
+
+
+def lib():
+    """Load libdpd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdpd.so is not built (run paper_1311_0402_gb300.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        i32, i64, u32, u64, f64, vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_double, ctypes.c_void_p)
+        L.dpd_default_options.argtypes = [P(dpd_options)]
+        L.dpd_default_options.restype = None
+        L.dpd_create.argtypes = [P(vp), P(f64), i32, P(f64), f64, f64, f64, f64, f64, P(dpd_options)]
+        L.dpd_set_state.argtypes = [vp, i64, P(f64), P(f64), P(i32), P(u32), u64]
+        L.dpd_set_bonds.argtypes = [vp, i64, P(u32), f64, f64]
+        L.dpd_build_neighbors.argtypes = [vp]
+        L.dpd_get_neighbors.argtypes = [vp, i64, P(u32), P(i64)]
+        L.dpd_forces.argtypes = [vp, P(f64)]
+        L.dpd_get_force.argtypes = [vp, P(f64)]
+        L.dpd_step.argtypes = [vp, i64]
+        L.dpd_observables.argtypes = [vp, P(dpd_obs)]
+        L.dpd_step_profiled.argtypes = [vp, i64, P(dpd_step_times)]
+        L.dpd_profile.argtypes = [vp, i32, i32, i32, P(f64), P(f64)]
+        L.dpd_get_state.argtypes = [vp, P(f64), P(f64), P(u64)]
+        L.dpd_info.argtypes = [vp, P(i64), P(i64), P(i32)]
+        L.dpd_pair_rng.argtypes = [u64, u64, i64, P(u32), P(u32), P(u32), P(ctypes.c_float)]
+        L.dpd_last_error.argtypes = [vp]
+        L.dpd_last_error.restype = ctypes.c_char_p
+        L.dpd_destroy.argtypes = [vp]
+        L.dpd_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _check(st, h=None):
+    if st != DPD_OK:
+        msg = lib().dpd_last_error(h)
+        raise DPDError(st, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------- C-named wrappers
+def dpd_default_options() -> dpd_options:
+    o = dpd_options()
+    lib().dpd_default_options(ctypes.byref(o))
+    return o
+
+
+def dpd_create(box, a_ij, gamma, kT, rc, s, dt, opt: dpd_options | None = None):
+    a = np.ascontiguousarray(np.atleast_2d(np.asarray(a_ij, np.float64)))
+    b = np.ascontiguousarray(np.asarray(box, np.float64))
+    h = ctypes.c_void_p()
+    st = lib().dpd_create(ctypes.byref(h), _p(b, ctypes.c_double), a.shape[0], _p(a, ctypes.c_double), gamma, kT, rc,
+                          s, dt, ctypes.byref(opt) if opt is not None else None)
+    _check(st)
+    return h
+
+
+def dpd_set_state(h, x, v, species=None, tag=None, step=0):
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, np.float64).reshape(-1, 3)
+    sp = None if species is None else np.ascontiguousarray(species, np.int32)
+    tg = None if tag is None else np.ascontiguousarray(tag, np.uint32)
+    _check(lib().dpd_set_state(h, x.shape[0], _p(x, ctypes.c_double), _p(v, ctypes.c_double),
+                               _p(sp, ctypes.c_int32), _p(tg, ctypes.c_uint32), step), h)
+
+
+def dpd_set_bonds(h, pairs, k, r0):
+    pr = np.ascontiguousarray(np.asarray(pairs, np.uint32).reshape(-1, 2))
+    _check(lib().dpd_set_bonds(h, pr.shape[0], _p(pr, ctypes.c_uint32), k, r0), h)
+
+
+def dpd_build_neighbors(h):
+    _check(lib().dpd_build_neighbors(h), h)
+
+
+def dpd_get_neighbors(h) -> np.ndarray:
+    cnt = ctypes.c_int64(0)
+    _check(lib().dpd_get_neighbors(h, 0, None, ctypes.byref(cnt)), h)
+    out = np.zeros((max(cnt.value, 1), 2), np.uint32)
+    _check(lib().dpd_get_neighbors(h, cnt.value, _p(out, ctypes.c_uint32), ctypes.byref(cnt)), h)
+    return out[:cnt.value]
+
+
+def dpd_info(h):
+    n, r, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().dpd_info(h, ctypes.byref(n), ctypes.byref(r), ctypes.byref(c)), h)
+    return dict(n=n.value, rebuilds=r.value, nbr_capacity=c.value)
+
+
+def _nvec(h):
+    return dpd_info(h)["n"]
+
+
+def dpd_forces(h) -> np.ndarray:
+    f = np.zeros((_nvec(h), 3), np.float64)
+    _check(lib().dpd_forces(h, _p(f, ctypes.c_double)), h)
+    return f
+
+
+def dpd_get_force(h) -> np.ndarray:
+    f = np.zeros((_nvec(h), 3), np.float64)
+    _check(lib().dpd_get_force(h, _p(f, ctypes.c_double)), h)
+    return f
+
+
+def dpd_step(h, nsteps: int):
+    _check(lib().dpd_step(h, int(nsteps)), h)
+
+
+def dpd_step_profiled(h, nsteps: int) -> dict:
+    t = dpd_step_times()
+    _check(lib().dpd_step_profiled(h, int(nsteps), ctypes.byref(t)), h)
+    return {k: getattr(t, k) for k, _ in dpd_step_times._fields_}
+
+
+def dpd_observables(h) -> dict:
+    o = dpd_obs()
+    _check(lib().dpd_observables(h, ctypes.byref(o)), h)
+    return dict(step=o.step, n=o.n, kinetic=o.kinetic, temperature=o.temperature, virial=o.virial,
+                pressure=o.pressure, momentum=np.array(list(o.momentum)))
+
+
+def dpd_profile(h, bin_axis: int, vel_axis: int, nbins: int, sums=None, counts=None):
+    s = np.zeros(nbins, np.float64) if sums is None else sums
+    c = np.zeros(nbins, np.float64) if counts is None else counts
+    _check(lib().dpd_profile(h, bin_axis, vel_axis, nbins, _p(s, ctypes.c_double), _p(c, ctypes.c_double)), h)
+    return s, c
+
+
+def dpd_get_state(h):
+    n = _nvec(h)
+    x = np.zeros((n, 3), np.float64)
+    v = np.zeros((n, 3), np.float64)
+    st = ctypes.c_uint64()
+    _check(lib().dpd_get_state(h, _p(x, ctypes.c_double), _p(v, ctypes.c_double), ctypes.byref(st)), h)
+    return x, v, st.value
+
+
+def dpd_pair_rng(seed: int, step: int, tag_i, tag_j):
+    ti = np.ascontiguousarray(tag_i, np.uint32)
+    tj = np.ascontiguousarray(tag_j, np.uint32)
+    m = ti.shape[0]
+    hh = np.zeros((max(m, 1), 2), np.uint32)
+    xi = np.zeros(max(m, 1), np.float32)
+    _check(lib().dpd_pair_rng(seed, step, m, _p(ti, ctypes.c_uint32), _p(tj, ctypes.c_uint32),
+                              _p(hh, ctypes.c_uint32), _p(xi, ctypes.c_float)))
+    return hh[:m], xi[:m]
+
+
+def dpd_last_error(h=None) -> str:
+    m = lib().dpd_last_error(h)
+    return m.decode() if m else ""
+
+
+def dpd_destroy(h):
+    lib().dpd_destroy(h)
+
+
+# -------------------------------------------------------------- convenience
+class Sim:
+    """A DPD system on the GPU (one handle of libdpd.so)."""
+
+    def __init__(self, box, a_ij, gamma, kT, rc, s, dt, lam=0.5, skin=0.3, seed=42, body_mode=0,
+                 body=(0.0, 0.0, 0.0), rebuild_every=0, nbr_capacity=0, graph_steps=8, stream=None):
+        o = dpd_default_options()
+        o.skin = skin
+        o.lam = lam
+        o.seed = seed
+        o.body_force_mode = body_mode
+        o.body_force[:] = [float(b) for b in body]
+        o.rebuild_every = rebuild_every
+        o.nbr_capacity = nbr_capacity
+        o.graph_steps = graph_steps
+        o.stream = stream
+        self.box = np.asarray(box, np.float64)
+        self.h = dpd_create(box, a_ij, gamma, kT, rc, s, dt, o)
+
+    def close(self):
+        if self.h is not None:
+            dpd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_state(self, x, v, species=None, tag=None, step=0):
+        dpd_set_state(self.h, x, v, species, tag, step)
+
+    def set_bonds(self, pairs, k, r0):
+        dpd_set_bonds(self.h, pairs, k, r0)
+
+    def build_neighbors(self):
+        dpd_build_neighbors(self.h)
+
+    def neighbors(self):
+        return dpd_get_neighbors(self.h)
+
+    def forces(self):
+        return dpd_forces(self.h)
+
+    def force(self):
+        return dpd_get_force(self.h)
+
+    def step(self, n):
+        dpd_step(self.h, n)
+
+    def step_profiled(self, n):
+        return dpd_step_profiled(self.h, n)
+
+    def observables(self):
+        return dpd_observables(self.h)
+
+    def profile(self, bin_axis, vel_axis, nbins, sums=None, counts=None):
+        return dpd_profile(self.h, bin_axis, vel_axis, nbins, sums, counts)
+
+    def state(self):
+        return dpd_get_state(self.h)
+
+    def info(self):
+        return dpd_info(self.h)

@@ -1,0 +1,119 @@
+// dpd_internal.cuh -- device data layout, parameter blocks and kernel
+// launchers shared by the translation units of libdpd.so.
+//
+// Layout (all particle arrays in cell order after a rebuild, double-buffered
+// so a rebuild can gather into the other set; a device word selects the
+// live set, so captured CUDA graphs never see a pointer change):
+//   pos[p]   float4 (x, y, z, species as int bits)      16 B
+//   vel[p]   float4 (vx, vy, vz, signature as u32 bits)  16 B  -- the velocity
+//            the pair force reads (v~ of the lambda scheme) and the
+//            particle's TEA signature for the current step (Sec. 3.5)
+//   vkick[p] float4 (v + dt/2 f) when lambda != 1/2      16 B
+//   force[p] float4 (fx, fy, fz, 0)                       16 B
+//   tag[p]   u32 identity tag (keys the random force)
+//   pid[p]   u32 caller's particle index
+// Neighbour list: tiles of 32 particles, column-major inside a tile
+// (nbr[(p/32)*cap*32 + k*32 + p%32]), so a warp reading its k-th
+// neighbours issues one 128-byte transaction (the transposed layout of
+// Sec. 3.3, written directly).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dpd {
+
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxBonds = 6;          // bonds per particle
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kStencil = 27;
+
+// device error bits
+constexpr uint32_t kErrNbrOverflow = 1u;
+constexpr uint32_t kErrNonFinite = 2u;
+
+struct DevCtl {
+    uint32_t parity;         // live buffer set
+    uint32_t rebuild;        // 1: the rebuild chain runs at its next launch
+    uint32_t err;            // error bits
+    uint32_t since_rebuild;  // steps since the last rebuild
+    unsigned long long step; // step number of the live state
+    unsigned long long nrebuild;
+    uint32_t max_nnb;        // largest neighbour count of the last build
+    uint32_t pad[3];
+};
+
+struct SimParams {
+    int n;
+    int ncell;
+    int nc[3];
+    int cap;                  // neighbour capacity per particle
+    float L[3];
+    float halfL[3];
+    float cells_per_len[3];   // nc / L
+    float rc2, rc, inv_rc;    // FP32 cutoff for the force decision
+    float rlist2;             // FP32 (rc + skin)^2 for the list
+    float gamma;
+    float sigma_isdt;         // sigma / sqrt(dt)
+    float s;
+    int s_mode;               // 1: s = 1, 2: s = 1/2, 3: s = 2, 0: general
+    float dt, half_dt, lambda_dt;
+    float disp2;              // (skin/2)^2 * 0.98^2: rebuild trigger
+    int lambda_half;          // lambda == 1/2 (vel holds v + dt/2 f)
+    int n_species;
+    int body_mode;
+    float body[3];
+    int rebuild_every;        // 0 = displacement only
+    uint32_t key[4];          // TEA key
+    float a[kMaxSpecies * kMaxSpecies];
+    float k_bond, r0_bond;
+    int has_bonds;
+};
+
+struct Ptrs {
+    float4 *pos[2], *vel[2], *vkick[2], *force[2];
+    uint32_t *tag[2], *pid[2];
+    float4 *xref;             // positions at the last rebuild
+    float4 *fout;             // output of a standalone force evaluation
+    DevCtl *ctl;
+    // cells
+    const uint32_t *rank_of_cell;  // (cz * nc_y + cy) * nc_x + cx -> Morton rank
+    const uint32_t *stencil;       // [ncell][27] neighbour ranks, ascending, kNone pad
+    uint32_t *cell_count;          // [ncell]
+    uint32_t *cell_start;          // [ncell + 1]
+    uint32_t *scan_part;           // block sums of the scan
+    uint32_t *key;                 // [n] cell rank per particle
+    uint32_t *slot;                // [n] arrival slot inside the cell
+    uint32_t *tmp_idx;             // [n] particle index in scatter order
+    unsigned long long *skey;      // [n] in-cell sort key in scatter order
+    uint32_t *perm;                // [n] new position -> old position
+    uint32_t *idx_of_pid;          // [n] caller index -> current position
+    // neighbours
+    uint32_t *nbr;                 // tiled list
+    uint32_t *nnb;                 // [n] counts
+    // bonds
+    const uint32_t *bond_partner;  // [n][kMaxBonds] partner caller indices
+    // reductions
+    double *red;                   // per-block partials
+};
+
+// ----------------------------------------------------------------- helpers
+__host__ __device__ inline uint32_t ceil_div_u(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
+
+// launchers (each returns the launch status)
+cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s);
+// mode 0: phase 1 from full-step v; 1: fused phase 2 + phase 1; 2: phase 2 only
+cudaError_t launch_integrate(const SimParams &P, const Ptrs &D, int mode, cudaStream_t s);
+cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, int n_scan_blocks);
+// out_fout: write into D.fout (standalone evaluation) instead of force[parity]
+// inc_step: the force kernel advances the device step counter (inside dpd_step)
+cudaError_t launch_force(const SimParams &P, const Ptrs &D, bool out_fout, bool inc_step, cudaStream_t s);
+cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s);
+cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int vel_axis, int nbins,
+                           int nblocks, cudaStream_t s);
+cudaError_t launch_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *ti, const uint32_t *tj,
+                            uint32_t *out_hash, float *out_xi, cudaStream_t s);
+int scan_blocks_for(int ncell);
+int observe_blocks_for(int n);
+
+}  // namespace dpd

@@ -1,0 +1,932 @@
+// engine.cu -- host engine and C ABI of libdpd.so (declared in dpd.h).
+//
+// Owns the device memory of a simulation, builds the cell geometry (Morton
+// ranks of the cells and the ascending 27-cell stencils, built once, as the
+// coarse stencil of Sec. 3.3.1), uploads and downloads particle state in the
+// caller's order, and drives the per-step kernel sequence of Algorithm 1:
+//   phase 1 (+ signature, displacement check) -> rebuild chain (runs only
+//   when flagged on the device) -> pair force -> phase 2,
+// captured into CUDA graphs of several steps that are replayed, so a step
+// costs no host round trip.  Host waits poll an event with a deadline.
+#include "dpd.h"
+#include "dpd_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+using namespace dpd;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Geometry {
+    int nc[3];
+    int ncell;
+    std::vector<uint32_t> rank_of_cell;  // linear (cz, cy, cx) -> rank
+    std::vector<uint32_t> stencil;       // [ncell][27]
+};
+
+uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
+{
+    uint32_t x = v & 0x3FFu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+void build_geometry(const int nc[3], Geometry &g)
+{
+    g.nc[0] = nc[0]; g.nc[1] = nc[1]; g.nc[2] = nc[2];
+    g.ncell = nc[0] * nc[1] * nc[2];
+    std::vector<std::pair<uint64_t, uint32_t>> order(g.ncell);
+    for (int z = 0; z < nc[2]; ++z)
+        for (int y = 0; y < nc[1]; ++y)
+            for (int x = 0; x < nc[0]; ++x) {
+                uint32_t lin = (uint32_t)((z * nc[1] + y) * nc[0] + x);
+                uint64_t code = (uint64_t)spread3((uint32_t)x) | ((uint64_t)spread3((uint32_t)y) << 1) |
+                                ((uint64_t)spread3((uint32_t)z) << 2);
+                order[lin] = {code, lin};
+            }
+    std::sort(order.begin(), order.end());
+    g.rank_of_cell.assign(g.ncell, 0);
+    std::vector<uint32_t> lin_of_rank(g.ncell);
+    for (int r = 0; r < g.ncell; ++r) {
+        g.rank_of_cell[order[r].second] = (uint32_t)r;
+        lin_of_rank[r] = order[r].second;
+    }
+    // distinct neighbour offsets per axis ({-1,0,1}, or fewer when an axis
+    // has fewer than three cells so no cell is listed twice)
+    std::vector<int> off[3];
+    for (int a = 0; a < 3; ++a) {
+        if (nc[a] >= 3) off[a] = {-1, 0, 1};
+        else if (nc[a] == 2) off[a] = {0, 1};
+        else off[a] = {0};
+    }
+    g.stencil.assign((size_t)g.ncell * kStencil, kNone);
+    std::vector<uint32_t> tmp;
+    for (int r = 0; r < g.ncell; ++r) {
+        uint32_t lin = lin_of_rank[r];
+        int x = lin % nc[0], y = (lin / nc[0]) % nc[1], z = lin / (nc[0] * nc[1]);
+        tmp.clear();
+        for (int oz : off[2])
+            for (int oy : off[1])
+                for (int ox : off[0]) {
+                    int cx = (x + ox + nc[0]) % nc[0], cy = (y + oy + nc[1]) % nc[1], cz = (z + oz + nc[2]) % nc[2];
+                    tmp.push_back(g.rank_of_cell[(cz * nc[1] + cy) * nc[0] + cx]);
+                }
+        std::sort(tmp.begin(), tmp.end());
+        std::copy(tmp.begin(), tmp.end(), g.stencil.begin() + (size_t)r * kStencil);
+    }
+}
+
+}  // namespace
+
+struct dpd_sim {
+    // parameters
+    double box[3];
+    int n_species;
+    std::vector<double> a;
+    double gamma, kT, rc, s, dt;
+    dpd_options opt;
+    SimParams P;
+    Ptrs D;
+    Geometry geo;
+    int n_scan_blocks = 0;
+    // device memory
+    std::vector<void *> allocs;        // per-n allocations
+    std::vector<void *> static_allocs; // geometry + control
+    int64_t n = 0;
+    int64_t cap_alloc_n = -1;
+    size_t red_doubles = 0;
+    bool has_state = false;
+    bool failed = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;  // steps per graph -> executable
+    std::map<int64_t, cudaGraphExec_t> timed_graphs;  // profiled runs, by steps
+    std::vector<cudaEvent_t> tev;           // timing events
+    uint64_t step = 0;                       // host mirror of the device step
+    std::string err;
+    std::vector<uint32_t> bond_partner_host;
+    bool bonds_set = false;
+};
+
+namespace {
+
+dpd_status fail(dpd_sim *h, dpd_status st, const std::string &msg)
+{
+    if (h) {
+        h->err = msg;
+        if (st == DPD_ERR_CUDA) h->failed = true;
+    }
+    g_last_error = msg;
+    return st;
+}
+
+#define CUDA_TRY(h, call)                                                                             \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail((h), DPD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+dpd_status dev_alloc(dpd_sim *h, void **p, size_t bytes, std::vector<void *> &list)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DPD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    list.push_back(*p);
+    return DPD_OK;
+}
+
+void free_list(std::vector<void *> &list)
+{
+    for (void *p : list) cudaFree(p);
+    list.clear();
+}
+
+// Wait for the stream with a deadline (no unbounded host spin).
+dpd_status wait(dpd_sim *h)
+{
+    cudaError_t e = cudaEventRecord(h->ev, h->stream);
+    if (e != cudaSuccess) return fail(h, DPD_ERR_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+    auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        e = cudaEventQuery(h->ev);
+        if (e == cudaSuccess) return DPD_OK;
+        if (e != cudaErrorNotReady) return fail(h, DPD_ERR_CUDA, std::string("kernel failure: ") + cudaGetErrorString(e));
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > h->opt.wait_timeout_s)
+            return fail(h, DPD_ERR_TIMEOUT, "GPU did not finish within " + std::to_string(h->opt.wait_timeout_s) + " s");
+        if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+dpd_status read_ctl(dpd_sim *h, DevCtl &c)
+{
+    CUDA_TRY(h, cudaMemcpyAsync(&c, h->D.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
+    return wait(h);
+}
+
+dpd_status check_err(dpd_sim *h, DevCtl &c)
+{
+    dpd_status st = read_ctl(h, c);
+    if (st) return st;
+    if (c.err & kErrNbrOverflow)
+        return fail(h, DPD_ERR_NBR_OVERFLOW,
+                    "neighbour list overflow: " + std::to_string(c.max_nnb) + " > capacity " + std::to_string(h->P.cap));
+    if (c.err & kErrNonFinite) return fail(h, DPD_ERR_NONFINITE, "non-finite force");
+    return DPD_OK;
+}
+
+void drop_graphs(dpd_sim *h)
+{
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    for (auto &kv : h->timed_graphs) cudaGraphExecDestroy(kv.second);
+    h->timed_graphs.clear();
+}
+
+constexpr int kRebuildKernels = 9;  // bin, 3 scan, scatter, rank, gather, commit, nbuild
+
+// Timing event on the stream; inside a graph capture it becomes an event
+// record node whose timestamp stays readable after the graph runs.
+cudaError_t rec(dpd_sim *h, cudaEvent_t e)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t err = cudaStreamIsCapturing(h->stream, &cs);
+    if (err != cudaSuccess) return err;
+    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+    return cudaEventRecord(e, h->stream);
+}
+
+// The kernel sequence of enqueue_steps with timing events between the
+// groups: ev[0] | integrate | ev[3s+1] | rebuild | ev[3s+2] | force | ev[3s+3] ... | P2 | ev[3k+1]
+cudaError_t enqueue_steps_timed(dpd_sim *h, int64_t k)
+{
+    cudaError_t e = rec(h, h->tev[0]);
+    for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
+        e = launch_integrate(h->P, h->D, s == 0 ? 0 : 1, h->stream);
+        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 1]);
+        if (e == cudaSuccess) e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
+        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 2]);
+        if (e == cudaSuccess) e = launch_force(h->P, h->D, false, true, h->stream);
+        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 3]);
+    }
+    if (e == cudaSuccess) e = launch_integrate(h->P, h->D, 2, h->stream);
+    if (e == cudaSuccess) e = rec(h, h->tev[3 * k + 1]);
+    return e;
+}
+
+// Kernel sequence of k steps (starting and ending at a full-step state).
+cudaError_t enqueue_steps(dpd_sim *h, int k)
+{
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < k && e == cudaSuccess; ++s) {
+        e = launch_integrate(h->P, h->D, s == 0 ? 0 : 1, h->stream);
+        if (e == cudaSuccess) e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
+        if (e == cudaSuccess) e = launch_force(h->P, h->D, false, true, h->stream);
+    }
+    if (e == cudaSuccess) e = launch_integrate(h->P, h->D, 2, h->stream);
+    return e;
+}
+
+dpd_status get_graph(dpd_sim *h, int k, cudaGraphExec_t *out)
+{
+    auto it = h->graphs.find(k);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return DPD_OK;
+    }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_steps(h, k);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(h, DPD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, DPD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    h->graphs[k] = ex;
+    *out = ex;
+    return DPD_OK;
+}
+
+int auto_capacity(const dpd_sim *h, int64_t n)
+{
+    double V = h->box[0] * h->box[1] * h->box[2];
+    double rl = h->rc + h->opt.skin;
+    double mean = (double)n / V * 4.0 / 3.0 * M_PI * rl * rl * rl;
+    int cap = (int)std::ceil(1.6 * mean + 24.0);
+    cap = (cap + 7) / 8 * 8;
+    return std::max(cap, 32);
+}
+
+dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
+{
+    drop_graphs(h);
+    free_list(h->allocs);
+    Ptrs &D = h->D;
+    const size_t f4 = sizeof(float4) * (size_t)n, u4 = sizeof(uint32_t) * (size_t)n;
+    dpd_status st = DPD_OK;
+    auto A = [&](void **p, size_t b) { if (st == DPD_OK) st = dev_alloc(h, p, b, h->allocs); };
+    for (int b = 0; b < 2; ++b) {
+        A((void **)&D.pos[b], f4);
+        A((void **)&D.vel[b], f4);
+        A((void **)&D.force[b], f4);
+        A((void **)&D.tag[b], u4);
+        A((void **)&D.pid[b], u4);
+        if (!h->P.lambda_half) A((void **)&D.vkick[b], f4);
+        else D.vkick[b] = nullptr;
+    }
+    A((void **)&D.xref, f4);
+    A((void **)&D.fout, f4);
+    A((void **)&D.key, u4);
+    A((void **)&D.slot, u4);
+    A((void **)&D.tmp_idx, u4);
+    A((void **)&D.skey, sizeof(unsigned long long) * (size_t)n);
+    A((void **)&D.perm, u4);
+    A((void **)&D.idx_of_pid, u4);
+    A((void **)&D.nnb, u4);
+    const size_t tiles = (size_t)(n + 31) / 32;
+    A((void **)&D.nbr, tiles * 32 * (size_t)cap * sizeof(uint32_t));
+    h->red_doubles = std::max<size_t>((size_t)observe_blocks_for((int)n) * 8, 4096);
+    A((void **)&D.red, h->red_doubles * sizeof(double));
+    A((void **)&D.bond_partner, sizeof(uint32_t) * (size_t)n * kMaxBonds);
+    if (st) return st;
+    CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(D.nnb, 0, u4, h->stream));
+    h->P.cap = cap;
+    h->cap_alloc_n = n;
+    return DPD_OK;
+}
+
+// Force a rebuild and a force evaluation at the current state (no step).
+dpd_status rebuild_and_force(dpd_sim *h, bool grow_on_overflow)
+{
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        uint32_t one = 1u;
+        CUDA_TRY(h, cudaMemcpyAsync(&h->D.ctl->rebuild, &one, sizeof(one), cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+        CUDA_TRY(h, launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks));
+        CUDA_TRY(h, launch_force(h->P, h->D, false, false, h->stream));
+        DevCtl c;
+        dpd_status st = check_err(h, c);
+        if (st != DPD_ERR_NBR_OVERFLOW || !grow_on_overflow) return st;
+        // grow the list: keep the particle arrays, reallocate the table
+        int cap = (int)((c.max_nnb * 5 / 4 + 16 + 7) / 8 * 8);
+        cudaFree(h->D.nbr);
+        h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->D.nbr));
+        st = dev_alloc(h, (void **)&h->D.nbr, (size_t)(h->n + 31) / 32 * 32 * (size_t)cap * sizeof(uint32_t), h->allocs);
+        if (st) return st;
+        h->P.cap = cap;
+        drop_graphs(h);
+    }
+    return fail(h, DPD_ERR_NBR_OVERFLOW, "neighbour list overflow after regrowing");
+}
+
+dpd_status guard(dpd_sim *h, bool need_state)
+{
+    if (!h) return fail(nullptr, DPD_ERR_ARG, "null handle");
+    if (h->failed) return fail(h, DPD_ERR_CUDA, "handle has a latched CUDA failure: " + h->err);
+    if (need_state && !h->has_state) return fail(h, DPD_ERR_STATE, "no particle state: call dpd_set_state first");
+    return DPD_OK;
+}
+
+// Download a float4 array and its caller indices; scatter xyz into out (n x 3).
+dpd_status download_xyz(dpd_sim *h, const float4 *dev, double *out)
+{
+    std::vector<float4> buf(h->n);
+    std::vector<uint32_t> pid(h->n);
+    DevCtl c;
+    dpd_status st = read_ctl(h, c);
+    if (st) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(buf.data(), dev, sizeof(float4) * h->n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.parity], sizeof(uint32_t) * h->n, cudaMemcpyDeviceToHost,
+                                h->stream));
+    st = wait(h);
+    if (st) return st;
+    for (int64_t p = 0; p < h->n; ++p) {
+        uint32_t i = pid[p];
+        out[3 * (size_t)i] = buf[p].x;
+        out[3 * (size_t)i + 1] = buf[p].y;
+        out[3 * (size_t)i + 2] = buf[p].z;
+    }
+    return DPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dpd_default_options(dpd_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->skin = 0.3;
+    o->rebuild_every = 0;
+    o->body_force_mode = 0;
+    o->seed = 42;
+    o->lambda = 0.5;
+    o->nbr_capacity = 0;
+    o->graph_steps = 8;
+    o->wait_timeout_s = 600.0;
+    o->stream = nullptr;
+}
+
+dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, const double *a_ij, double gamma,
+                      double kT, double rc, double s, double dt, const dpd_options *opt)
+{
+    if (!out) return fail(nullptr, DPD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    dpd_options o;
+    dpd_default_options(&o);
+    if (opt) o = *opt;
+    if (!box || !a_ij) return fail(nullptr, DPD_ERR_ARG, "box and a_ij are required");
+    if (!(rc > 0) || !(dt > 0) || !(kT >= 0) || !(gamma >= 0) || !(s > 0) || !(o.skin >= 0) || !std::isfinite(rc) ||
+        !std::isfinite(dt) || !std::isfinite(kT) || !std::isfinite(gamma) || !std::isfinite(s))
+        return fail(nullptr, DPD_ERR_ARG, "need rc > 0, dt > 0, kT >= 0, gamma >= 0, s > 0, skin >= 0");
+    if (n_species < 1 || n_species > kMaxSpecies) return fail(nullptr, DPD_ERR_ARG, "n_species must be in 1..8");
+    for (int i = 0; i < n_species; ++i)
+        for (int j = 0; j < n_species; ++j) {
+            double x = a_ij[i * n_species + j];
+            if (!std::isfinite(x) || x != a_ij[j * n_species + i])
+                return fail(nullptr, DPD_ERR_ARG, "a_ij must be finite and symmetric");
+        }
+    if (o.body_force_mode < 0 || o.body_force_mode > 2) return fail(nullptr, DPD_ERR_ARG, "body_force_mode in 0..2");
+    if (o.rebuild_every < 0 || o.graph_steps < 0 || o.nbr_capacity < 0 || !(o.wait_timeout_s > 0))
+        return fail(nullptr, DPD_ERR_ARG, "rebuild_every, graph_steps, nbr_capacity >= 0; wait_timeout_s > 0");
+    const double rl = rc + o.skin;
+    int nc[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 2.0 * rl) || !std::isfinite(box[a]))
+            return fail(nullptr, DPD_ERR_ARG, "each box length must exceed 2 (rc + skin)");
+        // cell side >= r_list (1 + 1e-4): the margin covers the FP32
+        // rounding of the cell index and of the pair predicate
+        nc[a] = std::max(1, (int)std::floor(box[a] / (rl * (1.0 + 1e-4))));
+        if (nc[a] > 1024) return fail(nullptr, DPD_ERR_ARG, "more than 1024 cells along an axis");
+    }
+    if ((int64_t)nc[0] * nc[1] * nc[2] >= (1 << 26)) return fail(nullptr, DPD_ERR_ARG, "too many cells");
+
+    dpd_sim *h = new dpd_sim();
+    std::memcpy(h->box, box, sizeof(h->box));
+    h->n_species = n_species;
+    h->a.assign(a_ij, a_ij + n_species * n_species);
+    h->gamma = gamma; h->kT = kT; h->rc = rc; h->s = s; h->dt = dt;
+    h->opt = o;
+    SimParams &P = h->P;
+    std::memset(&P, 0, sizeof(P));
+    for (int a = 0; a < 3; ++a) {
+        P.nc[a] = nc[a];
+        P.L[a] = (float)box[a];
+        P.halfL[a] = 0.5f * P.L[a];
+        P.cells_per_len[a] = (float)(nc[a] / box[a]);
+        P.body[a] = (float)o.body_force[a];
+    }
+    P.ncell = nc[0] * nc[1] * nc[2];
+    const float rcf = (float)rc, rlf = (float)rl;
+    P.rc = rcf;
+    P.rc2 = rcf * rcf;
+    P.inv_rc = (float)(1.0 / rc);
+    P.rlist2 = rlf * rlf;
+    P.gamma = (float)gamma;
+    P.sigma_isdt = (float)(std::sqrt(2.0 * gamma * kT) / std::sqrt(dt));
+    P.s = (float)s;
+    P.s_mode = s == 1.0 ? 1 : (s == 0.5 ? 2 : (s == 2.0 ? 3 : 0));
+    P.dt = (float)dt;
+    P.half_dt = (float)(0.5 * dt);
+    P.lambda_dt = (float)(o.lambda * dt);
+    P.lambda_half = o.lambda == 0.5 ? 1 : 0;
+    const double hs = 0.5 * o.skin * 0.98;  // 2 % margin against FP32 rounding
+    P.disp2 = (float)(hs * hs);
+    P.n_species = n_species;
+    for (int k = 0; k < n_species * n_species; ++k) P.a[k] = (float)a_ij[k];
+    P.body_mode = o.body_force_mode;
+    P.rebuild_every = o.rebuild_every;
+    P.key[0] = (uint32_t)(o.seed & 0xFFFFFFFFull);
+    P.key[1] = (uint32_t)(o.seed >> 32);
+    P.key[2] = 0x243F6A88u;
+    P.key[3] = 0x85A308D3u;
+
+    // stream and control block
+    if (o.stream) {
+        h->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(nullptr, DPD_ERR_CUDA, "cudaStreamCreate failed (no GPU?)");
+        }
+        h->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        dpd_destroy(h);
+        return fail(nullptr, DPD_ERR_CUDA, "cudaEventCreate failed");
+    }
+    build_geometry(nc, h->geo);
+    h->n_scan_blocks = scan_blocks_for(P.ncell);
+    dpd_status st = DPD_OK;
+    auto A = [&](void **p, size_t b) { if (st == DPD_OK) st = dev_alloc(h, p, b, h->static_allocs); };
+    A((void **)&h->D.ctl, sizeof(DevCtl));
+    A((void **)&h->D.rank_of_cell, sizeof(uint32_t) * P.ncell);
+    A((void **)&h->D.stencil, sizeof(uint32_t) * (size_t)P.ncell * kStencil);
+    A((void **)&h->D.cell_count, sizeof(uint32_t) * P.ncell);
+    A((void **)&h->D.cell_start, sizeof(uint32_t) * (P.ncell + 1));
+    A((void **)&h->D.scan_part, sizeof(uint32_t) * (h->n_scan_blocks + 1));
+    if (st) {
+        std::string m = h->err;
+        dpd_destroy(h);
+        return fail(nullptr, st, m);
+    }
+    cudaError_t e = cudaMemcpyAsync((void *)h->D.rank_of_cell, h->geo.rank_of_cell.data(), sizeof(uint32_t) * P.ncell,
+                                    cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)h->D.stencil, h->geo.stencil.data(), sizeof(uint32_t) * (size_t)P.ncell * kStencil,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->D.cell_count, 0, sizeof(uint32_t) * P.ncell, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->D.ctl, 0, sizeof(DevCtl), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        dpd_destroy(h);
+        return fail(nullptr, DPD_ERR_CUDA, std::string("upload of cell tables: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return DPD_OK;
+}
+
+dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v, const int32_t *species,
+                         const uint32_t *tag, uint64_t step)
+{
+    dpd_status st = guard(h, false);
+    if (st) return st;
+    if (n <= 0 || n >= (int64_t)1 << 31 || !x || !v) return fail(h, DPD_ERR_ARG, "need 0 < n < 2^31 and x, v");
+    std::vector<float4> pos(n), vel(n);
+    std::vector<uint32_t> tg(n), pid(n);
+    for (int64_t i = 0; i < n; ++i) {
+        float xf[3];
+        for (int a = 0; a < 3; ++a) {
+            double xv = x[3 * i + a], vv = v[3 * i + a];
+            if (!std::isfinite(xv) || !std::isfinite(vv)) return fail(h, DPD_ERR_ARG, "non-finite x or v");
+            double w = xv - h->box[a] * std::floor(xv / h->box[a]);
+            float f = (float)w;
+            if (!(f < h->P.L[a])) f = 0.0f;  // rounded up to L: the same point as 0
+            if (f < 0.0f) f = 0.0f;
+            xf[a] = f;
+        }
+        int sp = species ? species[i] : 0;
+        if (sp < 0 || sp >= h->n_species) return fail(h, DPD_ERR_ARG, "species out of range");
+        float spf;
+        std::memcpy(&spf, &sp, sizeof(spf));  // species travels as int bits in pos.w
+        pos[i] = make_float4(xf[0], xf[1], xf[2], spf);
+        vel[i] = make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.0f);
+        tg[i] = tag ? tag[i] : (uint32_t)i;
+        pid[i] = (uint32_t)i;
+    }
+    if (tag) {
+        std::vector<uint32_t> s(tg);
+        std::sort(s.begin(), s.end());
+        if (std::adjacent_find(s.begin(), s.end()) != s.end()) return fail(h, DPD_ERR_ARG, "tags must be distinct");
+    }
+    int cap = h->opt.nbr_capacity > 0 ? h->opt.nbr_capacity : auto_capacity(h, n);
+    if (n != h->n || cap != h->P.cap || h->cap_alloc_n != n) {
+        h->n = n;
+        h->P.n = (int)n;
+        st = alloc_particles(h, n, cap);
+        if (st) {
+            h->has_state = false;
+            return st;
+        }
+    }
+    h->has_state = false;
+    h->bonds_set = false;
+    h->P.has_bonds = 0;
+    drop_graphs(h);
+    Ptrs &D = h->D;
+    CUDA_TRY(h, cudaMemcpyAsync(D.pos[0], pos.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(D.vel[0], vel.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(D.force[0], 0, sizeof(float4) * n, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(D.tag[0], tg.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(D.pid[0], pid.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
+    if (!h->P.lambda_half) CUDA_TRY(h, cudaMemsetAsync(D.vkick[0], 0, sizeof(float4) * n, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
+    DevCtl c;
+    std::memset(&c, 0, sizeof(c));
+    c.step = step;
+    CUDA_TRY(h, cudaMemcpyAsync(D.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, launch_signature(h->P, D, h->stream));
+    h->step = step;
+    st = rebuild_and_force(h, h->opt.nbr_capacity == 0);
+    if (st) return st;
+    h->has_state = true;
+    return DPD_OK;
+}
+
+dpd_status dpd_set_bonds(dpd_sim *h, int64_t nb, const uint32_t *pairs, double k, double r0)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (nb < 0 || (nb > 0 && !pairs) || !std::isfinite(k) || !std::isfinite(r0))
+        return fail(h, DPD_ERR_ARG, "invalid bond arguments");
+    std::vector<uint32_t> bp((size_t)h->n * kMaxBonds, kNone);
+    std::vector<int> deg(h->n, 0);
+    for (int64_t b = 0; b < nb; ++b) {
+        uint32_t i = pairs[2 * b], j = pairs[2 * b + 1];
+        if (i >= (uint64_t)h->n || j >= (uint64_t)h->n || i == j) return fail(h, DPD_ERR_ARG, "bond index out of range");
+        if (deg[i] >= kMaxBonds || deg[j] >= kMaxBonds) return fail(h, DPD_ERR_ARG, "more than 6 bonds on a particle");
+        bp[(size_t)i * kMaxBonds + deg[i]++] = j;
+        bp[(size_t)j * kMaxBonds + deg[j]++] = i;
+    }
+    CUDA_TRY(h, cudaMemcpyAsync((void *)h->D.bond_partner, bp.data(), sizeof(uint32_t) * bp.size(),
+                                cudaMemcpyHostToDevice, h->stream));
+    h->P.has_bonds = nb > 0 ? 1 : 0;
+    h->P.k_bond = (float)k;
+    h->P.r0_bond = (float)r0;
+    h->bonds_set = nb > 0;
+    drop_graphs(h);
+    CUDA_TRY(h, launch_force(h->P, h->D, false, false, h->stream));
+    DevCtl c;
+    return check_err(h, c);
+}
+
+dpd_status dpd_build_neighbors(dpd_sim *h)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    return rebuild_and_force(h, h->opt.nbr_capacity == 0);
+}
+
+dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64_t *n_out)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (cap < 0 || (cap > 0 && !pairs_out) || !n_out) return fail(h, DPD_ERR_ARG, "invalid output arguments");
+    DevCtl c;
+    st = read_ctl(h, c);
+    if (st) return st;
+    const int64_t n = h->n;
+    const size_t tiles = (size_t)(n + 31) / 32;
+    std::vector<uint32_t> nbr(tiles * 32 * (size_t)h->P.cap), nnb(n), pid(n);
+    CUDA_TRY(h, cudaMemcpyAsync(nbr.data(), h->D.nbr, sizeof(uint32_t) * nbr.size(), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(nnb.data(), h->D.nnb, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.parity], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    st = wait(h);
+    if (st) return st;
+    std::vector<uint64_t> pr;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t *row = nbr.data() + (size_t)(i >> 5) * h->P.cap * 32 + (i & 31);
+        for (uint32_t k = 0; k < nnb[i]; ++k) {
+            uint32_t j = row[(size_t)k * 32];
+            if (j >= (uint32_t)n) return fail(h, DPD_ERR_STATE, "neighbour index out of range");
+            uint32_t a = pid[i], b = pid[j];
+            if (a < b) pr.push_back(((uint64_t)a << 32) | b);
+        }
+    }
+    std::sort(pr.begin(), pr.end());
+    pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+    *n_out = (int64_t)pr.size();
+    for (int64_t k = 0; k < cap && k < (int64_t)pr.size(); ++k) {
+        pairs_out[2 * k] = (uint32_t)(pr[k] >> 32);
+        pairs_out[2 * k + 1] = (uint32_t)(pr[k] & 0xFFFFFFFFu);
+    }
+    return DPD_OK;
+}
+
+dpd_status dpd_forces(dpd_sim *h, double *f_out)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+    CUDA_TRY(h, launch_force(h->P, h->D, true, false, h->stream));
+    DevCtl c;
+    st = check_err(h, c);
+    if (st) return st;
+    if (!f_out) return DPD_OK;
+    return download_xyz(h, h->D.fout, f_out);
+}
+
+dpd_status dpd_get_force(dpd_sim *h, double *f_out)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (!f_out) return fail(h, DPD_ERR_ARG, "f_out is NULL");
+    DevCtl c;
+    st = read_ctl(h, c);
+    if (st) return st;
+    return download_xyz(h, h->D.force[c.parity], f_out);
+}
+
+dpd_status dpd_step(dpd_sim *h, int64_t nsteps)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (nsteps < 0) return fail(h, DPD_ERR_ARG, "nsteps < 0");
+    if (nsteps == 0) return DPD_OK;
+    CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+    const int K = h->opt.graph_steps;
+    int64_t left = nsteps;
+    if (K > 0) {
+        cudaGraphExec_t gx;
+        st = get_graph(h, K, &gx);
+        if (st) return st;
+        while (left >= K) {
+            CUDA_TRY(h, cudaGraphLaunch(gx, h->stream));
+            left -= K;
+        }
+        if (left > 0) {
+            st = get_graph(h, (int)left, &gx);
+            if (st) return st;
+            CUDA_TRY(h, cudaGraphLaunch(gx, h->stream));
+            left = 0;
+        }
+    } else {
+        CUDA_TRY(h, enqueue_steps(h, (int)left));
+    }
+    h->step += (uint64_t)nsteps;
+    DevCtl c;
+    st = check_err(h, c);
+    if (st) {
+        h->has_state = st == DPD_ERR_TIMEOUT ? h->has_state : false;
+        return st;
+    }
+    return DPD_OK;
+}
+
+dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (nsteps < 1 || nsteps > 100000) return fail(h, DPD_ERR_ARG, "nsteps must be in 1..100000");
+    const size_t nev = (size_t)(3 * nsteps + 2);
+    while (h->tev.size() < nev) {
+        cudaEvent_t e;
+        CUDA_TRY(h, cudaEventCreate(&e));
+        h->tev.push_back(e);
+    }
+    DevCtl c0;
+    st = read_ctl(h, c0);
+    if (st) return st;
+    CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+    if (h->opt.graph_steps > 0) {
+        cudaGraphExec_t ex = nullptr;
+        auto it = h->timed_graphs.find(nsteps);
+        if (it != h->timed_graphs.end()) {
+            ex = it->second;
+        } else {
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_steps_timed(h, nsteps);
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return fail(h, DPD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e ? e : e2));
+            }
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(h, DPD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            h->timed_graphs[nsteps] = ex;
+        }
+        CUDA_TRY(h, cudaGraphLaunch(ex, h->stream));
+    } else {
+        CUDA_TRY(h, enqueue_steps_timed(h, nsteps));
+    }
+    h->step += (uint64_t)nsteps;
+    DevCtl c;
+    st = check_err(h, c);
+    if (st) {
+        h->has_state = false;
+        return st;
+    }
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        float ms = 0.f;
+        cudaError_t eerr = cudaSuccess;
+        auto el = [&](size_t a, size_t b) {
+            float t = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&t, h->tev[a], h->tev[b]);
+            if (e != cudaSuccess && eerr == cudaSuccess) eerr = e;
+            return (double)t;
+        };
+        for (int64_t s = 0; s < nsteps; ++s) {
+            out->integrate_ms += el(3 * s, 3 * s + 1);
+            out->rebuild_ms += el(3 * s + 1, 3 * s + 2);
+            out->force_ms += el(3 * s + 2, 3 * s + 3);
+        }
+        out->integrate_ms += el(3 * nsteps, 3 * nsteps + 1);
+        out->total_ms = el(0, 3 * nsteps + 1);
+        (void)ms;
+        if (eerr != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, DPD_ERR_STATE, std::string("event timing unavailable: ") + cudaGetErrorString(eerr));
+        }
+        out->steps = nsteps;
+        out->force_launches = nsteps;
+        out->kernel_launches = nsteps * (2 + kRebuildKernels) + 1;
+        out->rebuilds = (int64_t)(c.nrebuild - c0.nrebuild);
+    }
+    return DPD_OK;
+}
+
+dpd_status dpd_observables(dpd_sim *h, dpd_obs *out)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (!out) return fail(h, DPD_ERR_ARG, "out is NULL");
+    const int nb = observe_blocks_for((int)h->n);
+    CUDA_TRY(h, launch_observe(h->P, h->D, nb, h->stream));
+    std::vector<double> part((size_t)nb * 8);
+    CUDA_TRY(h, cudaMemcpyAsync(part.data(), h->D.red, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream));
+    DevCtl c;
+    CUDA_TRY(h, cudaMemcpyAsync(&c, h->D.ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    st = wait(h);
+    if (st) return st;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 8; ++k) acc[k] += part[(size_t)b * 8 + k];
+    const double V = h->box[0] * h->box[1] * h->box[2];
+    out->step = c.step;
+    out->n = h->n;
+    out->kinetic = 0.5 * acc[0];
+    out->temperature = h->n > 1 ? acc[0] / (3.0 * h->n - 3.0) : 0.0;
+    out->virial = acc[4];
+    out->pressure = (acc[0] + acc[4]) / (3.0 * V);
+    out->momentum[0] = acc[1];
+    out->momentum[1] = acc[2];
+    out->momentum[2] = acc[3];
+    return DPD_OK;
+}
+
+dpd_status dpd_profile(dpd_sim *h, int32_t bin_axis, int32_t vel_axis, int32_t nbins, double *sum_out,
+                       double *count_out)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (bin_axis < 0 || bin_axis > 2 || vel_axis < 0 || vel_axis > 2 || nbins < 1 || nbins > 100000 || !sum_out ||
+        !count_out)
+        return fail(h, DPD_ERR_ARG, "invalid profile arguments");
+    int nblocks = (int)std::min<int64_t>(std::max<int64_t>(1, h->n / 1024), 1024);
+    size_t need = (size_t)nblocks * 2 * nbins;
+    if (need > h->red_doubles) {
+        double *nr = nullptr;
+        st = dev_alloc(h, (void **)&nr, need * sizeof(double), h->allocs);
+        if (st) return st;
+        h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->D.red));
+        cudaFree(h->D.red);
+        h->D.red = nr;
+        h->red_doubles = need;
+        drop_graphs(h);
+    }
+    CUDA_TRY(h, launch_profile(h->P, h->D, bin_axis, vel_axis, nbins, nblocks, h->stream));
+    std::vector<double> part(need);
+    CUDA_TRY(h, cudaMemcpyAsync(part.data(), h->D.red, sizeof(double) * need, cudaMemcpyDeviceToHost, h->stream));
+    st = wait(h);
+    if (st) return st;
+    for (int b = 0; b < nblocks; ++b)
+        for (int k = 0; k < nbins; ++k) {
+            sum_out[k] += part[((size_t)b * nbins + k) * 2];
+            count_out[k] += part[((size_t)b * nbins + k) * 2 + 1];
+        }
+    return DPD_OK;
+}
+
+dpd_status dpd_get_state(dpd_sim *h, double *x, double *v, uint64_t *step)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    DevCtl c;
+    st = read_ctl(h, c);
+    if (st) return st;
+    if (x) {
+        st = download_xyz(h, h->D.pos[c.parity], x);
+        if (st) return st;
+    }
+    if (v) {
+        st = download_xyz(h, h->D.vel[c.parity], v);
+        if (st) return st;
+    }
+    if (step) *step = c.step;
+    return DPD_OK;
+}
+
+dpd_status dpd_info(dpd_sim *h, int64_t *n, int64_t *rebuilds, int32_t *nbr_capacity)
+{
+    dpd_status st = guard(h, false);
+    if (st) return st;
+    DevCtl c;
+    std::memset(&c, 0, sizeof(c));
+    if (h->has_state) {
+        st = read_ctl(h, c);
+        if (st) return st;
+    }
+    if (n) *n = h->n;
+    if (rebuilds) *rebuilds = (int64_t)c.nrebuild;
+    if (nbr_capacity) *nbr_capacity = h->P.cap;
+    return DPD_OK;
+}
+
+dpd_status dpd_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *tag_i, const uint32_t *tag_j,
+                        uint32_t *out_hash, float *out_xi)
+{
+    if (m < 0 || (m > 0 && (!tag_i || !tag_j || !out_hash))) return fail(nullptr, DPD_ERR_ARG, "invalid arguments");
+    if (m == 0) return DPD_OK;
+    cudaStream_t s = nullptr;
+    uint32_t *dti = nullptr, *dtj = nullptr, *dh = nullptr;
+    float *dx = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&dti, sizeof(uint32_t) * m);
+    if (e == cudaSuccess) e = cudaMalloc(&dtj, sizeof(uint32_t) * m);
+    if (e == cudaSuccess) e = cudaMalloc(&dh, sizeof(uint32_t) * 2 * m);
+    if (e == cudaSuccess && out_xi) e = cudaMalloc(&dx, sizeof(float) * m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dti, tag_i, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dtj, tag_j, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_pair_rng(seed, step, m, dti, dtj, dh, dx, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_hash, dh, sizeof(uint32_t) * 2 * m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && out_xi) e = cudaMemcpyAsync(out_xi, dx, sizeof(float) * m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dti); cudaFree(dtj); cudaFree(dh); cudaFree(dx);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, DPD_ERR_CUDA, std::string("dpd_pair_rng: ") + cudaGetErrorString(e));
+    }
+    return DPD_OK;
+}
+
+const char *dpd_last_error(const dpd_sim *h)
+{
+    if (h) return h->err.c_str();
+    return g_last_error.c_str();
+}
+
+void dpd_destroy(dpd_sim *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    free_list(h->allocs);
+    free_list(h->static_allocs);
+    for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+    if (h->ev) cudaEventDestroy(h->ev);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"
