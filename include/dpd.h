@@ -182,6 +182,56 @@ dpd_status dpd_info(dpd_sim *h, int64_t *n, int64_t *rebuilds, int32_t *nbr_capa
 dpd_status dpd_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *tag_i,
                         const uint32_t *tag_j, uint32_t *out_hash, float *out_xi);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free pair force (this entry point has no counterpart in the
+ * paper; it exists for callers that cannot allocate device memory: an
+ * application that owns all GPU memory through its own pool or allocator, a
+ * plug-in running inside another framework's memory budget, or code in a
+ * context where cudaMalloc is not permitted).  The caller passes device
+ * inputs and outputs it already owns; the library allocates nothing.
+ * ------------------------------------------------------------------------- */
+
+/* Parameters of dpd_forces_static (the same physics as dpd_create). */
+typedef struct {
+    double box[3];           /* periodic box, each length > 2 rc */
+    int32_t n_species;       /* 1..8 */
+    int32_t body_force_mode; /* 0 none, 1 uniform, 2 +g for y < L_y/2 and -g above */
+    double a_ij[64];         /* n_species x n_species row-major, symmetric */
+    double gamma, kT, rc, s, dt;
+    uint64_t seed;           /* seed of the random force (TEA key) */
+    double body_force[3];
+} dpd_static_params;
+
+/* Total pair force (Eqs. 2-9, plus the body force; no bonds) on n particles
+ * at one step, with no device allocation.  All arrays are DEVICE pointers
+ * owned by the caller, in the caller's order:
+ *   pos:       n x 4 floats (x, y, z in [0, L), species as int bits)
+ *   vel:       n x 4 floats (vx, vy, vz, unused)
+ *   tag:       n identity tags keying the random force, or NULL (tag = index)
+ *   force_out: n x 4 floats (fx, fy, fz, 0)
+ * step keys the random force; stream is a cudaStream_t (NULL = default).
+ * The work is enqueued on the stream and the call returns without waiting:
+ * force_out is complete when the stream reaches that point.
+ * Scratch: one static device array of fixed size inside the library, which
+ * every GPU that loads the library holds until the process exits.  Limits:
+ * n <= dpd_forces_static_max_particles() (131072) and at most 65536 cells of
+ * side >= rc; larger inputs return DPD_ERR_ARG with a message and launch
+ * nothing.  The array's device address is looked up on the first call made
+ * on each device, so make that first call before any CUDA stream capture.
+ * Every call reuses the same array (the cell counts are cleared at the start
+ * of each call), so calls whose kernels overlap on the GPU -- on different
+ * streams, or from different host threads without ordering -- race on it.
+ * Errors: DPD_ERR_ARG for invalid or oversized input, DPD_ERR_CUDA for a
+ * failed launch; dpd_forces_static_last_error() describes the failure. */
+dpd_status dpd_forces_static(const dpd_static_params *params, int64_t n, const float *pos, const float *vel,
+                             const uint32_t *tag, uint64_t step, float *force_out, void *stream);
+
+/* Largest n dpd_forces_static accepts. */
+int64_t dpd_forces_static_max_particles(void);
+
+/* Description of the last dpd_forces_static failure on this host thread. */
+const char *dpd_forces_static_last_error(void);
+
 /* Description of the last failure on h (or of the last handle-less failure
  * when h is NULL).  Valid until the next call on h. */
 const char *dpd_last_error(const dpd_sim *h);

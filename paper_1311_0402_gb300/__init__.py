@@ -24,7 +24,8 @@ STATUS = {0: "DPD_OK", 1: "DPD_ERR_ARG", 2: "DPD_ERR_OOM", 3: "DPD_ERR_CUDA", 4:
 # every exported symbol declared in include/dpd.h
 EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds", "dpd_build_neighbors",
            "dpd_get_neighbors", "dpd_forces", "dpd_get_force", "dpd_step", "dpd_observables", "dpd_profile",
-           "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled")
+           "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled",
+           "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error")
 
 
 class DPDError(RuntimeError):
@@ -73,6 +74,22 @@ class dpd_step_times(ctypes.Structure):
     ]
 
 
+class dpd_static_params(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double * 3),
+        ("n_species", ctypes.c_int32),
+        ("body_force_mode", ctypes.c_int32),
+        ("a_ij", ctypes.c_double * 64),
+        ("gamma", ctypes.c_double),
+        ("kT", ctypes.c_double),
+        ("rc", ctypes.c_double),
+        ("s", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("body_force", ctypes.c_double * 3),
+    ]
+
+
 _lib = None
 
 
@@ -109,6 +126,11 @@ def lib():
         L.dpd_pair_rng.argtypes = [u64, u64, i64, P(u32), P(u32), P(u32), P(ctypes.c_float)]
         L.dpd_last_error.argtypes = [vp]
         L.dpd_last_error.restype = ctypes.c_char_p
+        L.dpd_forces_static.argtypes = [P(dpd_static_params), i64, vp, vp, vp, u64, vp, vp]
+        L.dpd_forces_static_max_particles.argtypes = []
+        L.dpd_forces_static_max_particles.restype = i64
+        L.dpd_forces_static_last_error.argtypes = []
+        L.dpd_forces_static_last_error.restype = ctypes.c_char_p
         L.dpd_destroy.argtypes = [vp]
         L.dpd_destroy.restype = None
         _lib = L
@@ -232,6 +254,39 @@ def dpd_pair_rng(seed: int, step: int, tag_i, tag_j):
     _check(lib().dpd_pair_rng(seed, step, m, _p(ti, ctypes.c_uint32), _p(tj, ctypes.c_uint32),
                               _p(hh, ctypes.c_uint32), _p(xi, ctypes.c_float)))
     return hh[:m], xi[:m]
+
+
+def dpd_static_params_from(box, a_ij, gamma, kT, rc, s, dt, seed=42, body_mode=0, body=(0.0, 0.0, 0.0)):
+    a = np.atleast_2d(np.asarray(a_ij, np.float64))
+    p = dpd_static_params()
+    p.box[:] = [float(b) for b in box]
+    p.n_species = a.shape[0]
+    p.body_force_mode = body_mode
+    p.a_ij[:a.size] = [float(x) for x in a.reshape(-1)]
+    p.gamma, p.kT, p.rc, p.s, p.dt = gamma, kT, rc, s, dt
+    p.seed = seed
+    p.body_force[:] = [float(b) for b in body]
+    return p
+
+
+def dpd_forces_static(params: dpd_static_params, n: int, pos_ptr: int, vel_ptr: int, tag_ptr, step: int,
+                      force_ptr: int, stream_ptr=None):
+    """Enqueue the allocation-free force on device pointers (see dpd.h)."""
+    st = lib().dpd_forces_static(ctypes.byref(params), int(n), ctypes.c_void_p(pos_ptr), ctypes.c_void_p(vel_ptr),
+                                 None if tag_ptr is None else ctypes.c_void_p(tag_ptr), int(step),
+                                 ctypes.c_void_p(force_ptr), None if stream_ptr is None else ctypes.c_void_p(stream_ptr))
+    if st != DPD_OK:
+        m = lib().dpd_forces_static_last_error()
+        raise DPDError(st, m.decode() if m else "")
+
+
+def dpd_forces_static_max_particles() -> int:
+    return int(lib().dpd_forces_static_max_particles())
+
+
+def dpd_forces_static_last_error() -> str:
+    m = lib().dpd_forces_static_last_error()
+    return m.decode() if m else ""
 
 
 def dpd_last_error(h=None) -> str:
