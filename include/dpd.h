@@ -141,9 +141,11 @@ dpd_status dpd_step(dpd_sim *h, int64_t nsteps);
  * the handle's stream around every kernel group of every step. */
 typedef struct {
     double total_ms;        /* first to last event */
-    double integrate_ms;    /* velocity-Verlet phases (+ signature, displacement check) */
+    double integrate_ms;    /* the opening velocity-Verlet phase 1 of the call */
     double rebuild_ms;      /* binning / scan / reorder / neighbour-list chain */
-    double force_ms;        /* fused pair force (+ bonds, body force) */
+    double force_ms;        /* fused pair force (+ bonds, body force, and the
+                               integration into the next step, which runs in
+                               the force kernel's epilogue) */
     int64_t steps;
     int64_t force_launches;
     int64_t kernel_launches;

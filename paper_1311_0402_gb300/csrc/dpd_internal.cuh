@@ -33,14 +33,16 @@ constexpr uint32_t kErrNbrOverflow = 1u;
 constexpr uint32_t kErrNonFinite = 2u;
 
 struct DevCtl {
-    uint32_t parity;         // live buffer set
+    uint32_t parity;         // live set of the state arrays (pos, vel, vkick, force)
     uint32_t rebuild;        // 1: the rebuild chain runs at its next launch
     uint32_t err;            // error bits
     uint32_t since_rebuild;  // steps since the last rebuild
     unsigned long long step; // step number of the live state
     unsigned long long nrebuild;
     uint32_t max_nnb;        // largest neighbour count of the last build
-    uint32_t pad[3];
+    uint32_t rebuild_next;   // displacement flags raised by the kernel running now
+    uint32_t done;           // finished blocks of the kernel running now
+    uint32_t oparity;        // live set of the order arrays (tag, pid): flips only at a rebuild
 };
 
 struct SimParams {
@@ -59,6 +61,7 @@ struct SimParams {
     int s_mode;               // 1: s = 1, 2: s = 1/2, 3: s = 2, 0: general
     float dt, half_dt, lambda_dt;
     float disp2;              // (skin/2)^2 * 0.98^2: rebuild trigger
+    float wrap_margin;        // r_list + skin + 0.01 if 2 x that < every L, else 0
     int lambda_half;          // lambda == 1/2 (vel holds v + dt/2 f)
     int n_species;
     int body_mode;
@@ -102,12 +105,16 @@ __host__ __device__ inline uint32_t ceil_div_u(uint32_t a, uint32_t b) { return 
 
 // launchers (each returns the launch status)
 cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s);
-// mode 0: phase 1 from full-step v; 1: fused phase 2 + phase 1; 2: phase 2 only
-cudaError_t launch_integrate(const SimParams &P, const Ptrs &D, int mode, cudaStream_t s);
+// velocity-Verlet phase 1 from the full-step velocity, in place
+cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s);
 cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, int n_scan_blocks);
-// out_fout: write into D.fout (standalone evaluation) instead of force[parity]
-// inc_step: the force kernel advances the device step counter (inside dpd_step)
-cudaError_t launch_force(const SimParams &P, const Ptrs &D, bool out_fout, bool inc_step, cudaStream_t s);
+// Pair force.  kForceEval: the force of the live state into D.fout (out_fout)
+// or force[parity], nothing else changes.  kForceStep: force at the live
+// state, then phase 2 of this step and phase 1 of the next into the other
+// buffer set (flips the live set, advances the step).  kForceFinish: force,
+// then phase 2 only (full-step velocity and force into the other set).
+enum ForceMode { kForceEval = 0, kForceStep = 1, kForceFinish = 2 };
+cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s);
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s);
 cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int vel_axis, int nbins,
                            int nblocks, cudaStream_t s);

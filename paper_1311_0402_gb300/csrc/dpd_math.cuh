@@ -13,12 +13,10 @@ namespace dpd {
 // agree bit for bit: d -= L if d > L/2, d += L if d < -L/2.
 __device__ __forceinline__ float min_image_rn(float xj, float xi, float L, float h)
 {
-    float t = __fsub_rn(xj, xi);
-    if (t > h)
-        t = __fsub_rn(t, L);
-    else if (t < -h)
-        t = __fadd_rn(t, L);
-    return t;
+    const float t = __fsub_rn(xj, xi);
+    const float tm = __fsub_rn(t, L);
+    const float tp = __fadd_rn(t, L);
+    return t > h ? tm : (t < -h ? tp : t);  // selects, no branches
 }
 
 // d^2 = (dx dx + dy dy) + dz dz, each product and sum rounded on its own.

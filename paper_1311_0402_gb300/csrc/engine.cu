@@ -216,33 +216,31 @@ cudaError_t rec(dpd_sim *h, cudaEvent_t e)
 }
 
 // The kernel sequence of enqueue_steps with timing events between the
-// groups: ev[0] | integrate | ev[3s+1] | rebuild | ev[3s+2] | force | ev[3s+3] ... | P2 | ev[3k+1]
+// groups: ev[0] | phase 1 | ev[1] | rebuild | ev[2] | force (+ integrate) | ev[3] | rebuild | ev[4] ...
 cudaError_t enqueue_steps_timed(dpd_sim *h, int64_t k)
 {
     cudaError_t e = rec(h, h->tev[0]);
+    if (e == cudaSuccess) e = launch_phase1(h->P, h->D, h->stream);
+    if (e == cudaSuccess) e = rec(h, h->tev[1]);
     for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
-        e = launch_integrate(h->P, h->D, s == 0 ? 0 : 1, h->stream);
-        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 1]);
-        if (e == cudaSuccess) e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
-        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 2]);
-        if (e == cudaSuccess) e = launch_force(h->P, h->D, false, true, h->stream);
-        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 3]);
+        e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
+        if (e == cudaSuccess) e = rec(h, h->tev[2 * s + 2]);
+        if (e == cudaSuccess) e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream);
+        if (e == cudaSuccess) e = rec(h, h->tev[2 * s + 3]);
     }
-    if (e == cudaSuccess) e = launch_integrate(h->P, h->D, 2, h->stream);
-    if (e == cudaSuccess) e = rec(h, h->tev[3 * k + 1]);
     return e;
 }
 
-// Kernel sequence of k steps (starting and ending at a full-step state).
+// Kernel sequence of k steps (starting and ending at a full-step state):
+// phase 1, then per step the rebuild chain (runs only when flagged) and the
+// force kernel, which integrates into the next step (or finishes the last).
 cudaError_t enqueue_steps(dpd_sim *h, int k)
 {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = launch_phase1(h->P, h->D, h->stream);
     for (int s = 0; s < k && e == cudaSuccess; ++s) {
-        e = launch_integrate(h->P, h->D, s == 0 ? 0 : 1, h->stream);
-        if (e == cudaSuccess) e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
-        if (e == cudaSuccess) e = launch_force(h->P, h->D, false, true, h->stream);
+        e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
+        if (e == cudaSuccess) e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream);
     }
-    if (e == cudaSuccess) e = launch_integrate(h->P, h->D, 2, h->stream);
     return e;
 }
 
@@ -327,7 +325,7 @@ dpd_status rebuild_and_force(dpd_sim *h, bool grow_on_overflow)
         CUDA_TRY(h, cudaMemcpyAsync(&h->D.ctl->rebuild, &one, sizeof(one), cudaMemcpyHostToDevice, h->stream));
         CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
         CUDA_TRY(h, launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks));
-        CUDA_TRY(h, launch_force(h->P, h->D, false, false, h->stream));
+        CUDA_TRY(h, launch_force(h->P, h->D, kForceEval, false, h->stream));
         DevCtl c;
         dpd_status st = check_err(h, c);
         if (st != DPD_ERR_NBR_OVERFLOW || !grow_on_overflow) return st;
@@ -360,7 +358,7 @@ dpd_status download_xyz(dpd_sim *h, const float4 *dev, double *out)
     dpd_status st = read_ctl(h, c);
     if (st) return st;
     CUDA_TRY(h, cudaMemcpyAsync(buf.data(), dev, sizeof(float4) * h->n, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.parity], sizeof(uint32_t) * h->n, cudaMemcpyDeviceToHost,
+    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.oparity], sizeof(uint32_t) * h->n, cudaMemcpyDeviceToHost,
                                 h->stream));
     st = wait(h);
     if (st) return st;
@@ -457,6 +455,11 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     P.lambda_half = o.lambda == 0.5 ? 1 : 0;
     const double hs = 0.5 * o.skin * 0.98;  // 2 % margin against FP32 rounding
     P.disp2 = (float)(hs * hs);
+    // a particle this far from every face has all its list neighbours on the
+    // same side of the periodic boundary (list radius + the most both ends
+    // can move before a rebuild + a rounding margin)
+    const double wm = rl + o.skin + 0.01;
+    P.wrap_margin = (2.0 * wm < box[0] && 2.0 * wm < box[1] && 2.0 * wm < box[2]) ? (float)wm : 0.0f;
     P.n_species = n_species;
     for (int k = 0; k < n_species * n_species; ++k) P.a[k] = (float)a_ij[k];
     P.body_mode = o.body_force_mode;
@@ -602,7 +605,7 @@ dpd_status dpd_set_bonds(dpd_sim *h, int64_t nb, const uint32_t *pairs, double k
     h->P.r0_bond = (float)r0;
     h->bonds_set = nb > 0;
     drop_graphs(h);
-    CUDA_TRY(h, launch_force(h->P, h->D, false, false, h->stream));
+    CUDA_TRY(h, launch_force(h->P, h->D, kForceEval, false, h->stream));
     DevCtl c;
     return check_err(h, c);
 }
@@ -627,7 +630,7 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
     std::vector<uint32_t> nbr(tiles * 32 * (size_t)h->P.cap), nnb(n), pid(n);
     CUDA_TRY(h, cudaMemcpyAsync(nbr.data(), h->D.nbr, sizeof(uint32_t) * nbr.size(), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(nnb.data(), h->D.nnb, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.parity], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.oparity], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
     st = wait(h);
     if (st) return st;
     std::vector<uint64_t> pr;
@@ -655,7 +658,7 @@ dpd_status dpd_forces(dpd_sim *h, double *f_out)
     dpd_status st = guard(h, true);
     if (st) return st;
     CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
-    CUDA_TRY(h, launch_force(h->P, h->D, true, false, h->stream));
+    CUDA_TRY(h, launch_force(h->P, h->D, kForceEval, true, h->stream));
     DevCtl c;
     st = check_err(h, c);
     if (st) return st;
@@ -715,7 +718,7 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
     dpd_status st = guard(h, true);
     if (st) return st;
     if (nsteps < 1 || nsteps > 100000) return fail(h, DPD_ERR_ARG, "nsteps must be in 1..100000");
-    const size_t nev = (size_t)(3 * nsteps + 2);
+    const size_t nev = (size_t)(2 * nsteps + 2);
     while (h->tev.size() < nev) {
         cudaEvent_t e;
         CUDA_TRY(h, cudaEventCreate(&e));
@@ -757,7 +760,6 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
     }
     if (out) {
         std::memset(out, 0, sizeof(*out));
-        float ms = 0.f;
         cudaError_t eerr = cudaSuccess;
         auto el = [&](size_t a, size_t b) {
             float t = 0.f;
@@ -765,21 +767,19 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
             if (e != cudaSuccess && eerr == cudaSuccess) eerr = e;
             return (double)t;
         };
+        out->integrate_ms = el(0, 1);
         for (int64_t s = 0; s < nsteps; ++s) {
-            out->integrate_ms += el(3 * s, 3 * s + 1);
-            out->rebuild_ms += el(3 * s + 1, 3 * s + 2);
-            out->force_ms += el(3 * s + 2, 3 * s + 3);
+            out->rebuild_ms += el(s == 0 ? 1 : 2 * s + 1, 2 * s + 2);
+            out->force_ms += el(2 * s + 2, 2 * s + 3);
         }
-        out->integrate_ms += el(3 * nsteps, 3 * nsteps + 1);
-        out->total_ms = el(0, 3 * nsteps + 1);
-        (void)ms;
+        out->total_ms = el(0, 2 * nsteps + 1);
         if (eerr != cudaSuccess) {
             cudaGetLastError();
             return fail(h, DPD_ERR_STATE, std::string("event timing unavailable: ") + cudaGetErrorString(eerr));
         }
         out->steps = nsteps;
         out->force_launches = nsteps;
-        out->kernel_launches = nsteps * (2 + kRebuildKernels) + 1;
+        out->kernel_launches = nsteps * (1 + kRebuildKernels) + 1;
         out->rebuilds = (int64_t)(c.nrebuild - c0.nrebuild);
     }
     return DPD_OK;

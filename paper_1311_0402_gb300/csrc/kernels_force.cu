@@ -21,84 +21,77 @@ __device__ __forceinline__ float wrap_pos(float x, float L, float invL)
     return x;
 }
 
-// Phase 1 of the step k -> k+1 from the full-step velocity, fused phase 2 of
-// step k + phase 1 of step k+1, or phase 2 alone (MODE 0 / 1 / 2):
-//   u = v + dt/2 f      (velocity at the half step)
-//   x += dt u           (= x + dt v + dt^2/2 f)
-//   v~ = v + lambda dt f  (the velocity the pair force sees; = u when
-//                          lambda = 1/2)
-//   v = u + dt/2 f'     (phase 2, after the new force f')
-// Phases 1 also compute the particle's signature for step k+1 and flag a
-// rebuild when the particle has moved more than skin/2 since the lists were
-// built.
-template <int MODE, bool LHALF>
-__global__ void k_integrate(SimParams P, Ptrs D)
+// End-of-block bookkeeping of the kernels that move particles.  Every block
+// reports whether one of its particles crossed the displacement threshold;
+// the last block to finish (all others have completed their reads and
+// writes) publishes the rebuild flag for the chain that follows and, when
+// `advance` is set, makes the buffer set it wrote the live one and advances
+// the step counter.
+__device__ __forceinline__ void finish_block(const SimParams &P, DevCtl *ctl, bool moved, bool advance, bool check_every)
 {
-    const DevCtl *ctl = D.ctl;
+    const bool any = __syncthreads_or(moved);
+    if (threadIdx.x == 0) {
+        if (any) atomicOr(&ctl->rebuild_next, 1u);
+        __threadfence();
+        const uint32_t prev = atomicAdd(&ctl->done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            uint32_t next = atomicExch(&ctl->rebuild_next, 0u);
+            if (check_every && P.rebuild_every > 0 && ctl->since_rebuild + 1u >= (uint32_t)P.rebuild_every) next = 1u;
+            ctl->rebuild = next;
+            ctl->done = 0u;
+            if (advance) {
+                ctl->parity ^= 1u;
+                ctl->step += 1ull;
+                ctl->since_rebuild += 1u;
+            }
+            __threadfence();
+        }
+    }
+}
+
+__device__ __forceinline__ bool moved_beyond(const SimParams &P, float4 x, float4 r)
+{
+    const float dx = min_image_rn(x.x, r.x, P.L[0], P.halfL[0]);
+    const float dy = min_image_rn(x.y, r.y, P.L[1], P.halfL[1]);
+    const float dz = min_image_rn(x.z, r.z, P.L[2], P.halfL[2]);
+    return dist2_rn(dx, dy, dz) > P.disp2;
+}
+
+// Phase 1 of the step k -> k+1 from the full-step velocity v (in place):
+//   u = v + dt/2 f,  x += dt u  (= x + dt v + dt^2/2 f),  v~ = v + lambda dt f
+// (v~ = u when lambda = 1/2), signature for step k+1, displacement check.
+template <bool LHALF>
+__global__ void k_phase1(SimParams P, Ptrs D)
+{
+    DevCtl *ctl = D.ctl;
     const uint32_t par = ctl->parity;
     const uint32_t step1 = (uint32_t)(ctl->step + 1ull);
     float4 *pos = D.pos[par];
     float4 *vel = D.vel[par];
-    float4 *vk = D.vkick[par];
     const float4 *frc = D.force[par];
-    const uint32_t *tag = D.tag[par];
+    const uint32_t *tag = D.tag[ctl->oparity];
     bool moved = false;
     const float invL[3] = {1.0f / P.L[0], 1.0f / P.L[1], 1.0f / P.L[2]};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        float4 f = frc[i];
-        float4 v = vel[i];
-        if (MODE == 2) {
-            float4 u = LHALF ? v : vk[i];
-            v.x = fmaf(P.half_dt, f.x, u.x);
-            v.y = fmaf(P.half_dt, f.y, u.y);
-            v.z = fmaf(P.half_dt, f.z, u.z);
-            vel[i] = v;  // signature word unchanged
-            continue;
-        }
-        float ux, uy, uz;   // new half-step velocity
-        float tx, ty, tz;   // v~
-        if (MODE == 0) {
-            ux = fmaf(P.half_dt, f.x, v.x);
-            uy = fmaf(P.half_dt, f.y, v.y);
-            uz = fmaf(P.half_dt, f.z, v.z);
-            tx = LHALF ? ux : fmaf(P.lambda_dt, f.x, v.x);
-            ty = LHALF ? uy : fmaf(P.lambda_dt, f.y, v.y);
-            tz = LHALF ? uz : fmaf(P.lambda_dt, f.z, v.z);
-        } else if (LHALF) {
-            // u' = u + dt f (phase 2 kick then phase 1 kick)
-            ux = fmaf(P.dt, f.x, v.x);
-            uy = fmaf(P.dt, f.y, v.y);
-            uz = fmaf(P.dt, f.z, v.z);
-            tx = ux; ty = uy; tz = uz;
-        } else {
-            float4 u = vk[i];
-            float vx = fmaf(P.half_dt, f.x, u.x), vy = fmaf(P.half_dt, f.y, u.y), vz = fmaf(P.half_dt, f.z, u.z);
-            ux = fmaf(P.half_dt, f.x, vx);
-            uy = fmaf(P.half_dt, f.y, vy);
-            uz = fmaf(P.half_dt, f.z, vz);
-            tx = fmaf(P.lambda_dt, f.x, vx);
-            ty = fmaf(P.lambda_dt, f.y, vy);
-            tz = fmaf(P.lambda_dt, f.z, vz);
-        }
+        const float4 f = frc[i];
+        const float4 v = vel[i];
+        const float ux = fmaf(P.half_dt, f.x, v.x), uy = fmaf(P.half_dt, f.y, v.y), uz = fmaf(P.half_dt, f.z, v.z);
         float4 x = pos[i];
         x.x = wrap_pos(fmaf(P.dt, ux, x.x), P.L[0], invL[0]);
         x.y = wrap_pos(fmaf(P.dt, uy, x.y), P.L[1], invL[1]);
         x.z = wrap_pos(fmaf(P.dt, uz, x.z), P.L[2], invL[2]);
         pos[i] = x;
-        uint32_t sig = signature(tag[i], step1, P.key);
-        vel[i] = make_float4(tx, ty, tz, __uint_as_float(sig));
-        if (!LHALF) vk[i] = make_float4(ux, uy, uz, 0.0f);
-        float4 r = D.xref[i];
-        float dx = min_image_rn(x.x, r.x, P.L[0], P.halfL[0]);
-        float dy = min_image_rn(x.y, r.y, P.L[1], P.halfL[1]);
-        float dz = min_image_rn(x.z, r.z, P.L[2], P.halfL[2]);
-        moved |= dist2_rn(dx, dy, dz) > P.disp2;
+        const float sig = __uint_as_float(signature(tag[i], step1, P.key));
+        if (LHALF) {
+            vel[i] = make_float4(ux, uy, uz, sig);
+        } else {
+            vel[i] = make_float4(fmaf(P.lambda_dt, f.x, v.x), fmaf(P.lambda_dt, f.y, v.y), fmaf(P.lambda_dt, f.z, v.z), sig);
+            D.vkick[par][i] = make_float4(ux, uy, uz, 0.0f);
+        }
+        moved |= moved_beyond(P, x, D.xref[i]);
     }
-    if (MODE != 2) {
-        bool any = __syncthreads_or(moved);
-        bool due = P.rebuild_every > 0 && ctl->since_rebuild + 1u >= (uint32_t)P.rebuild_every;
-        if (threadIdx.x == 0 && (any || (due && blockIdx.x == 0))) atomicOr(&D.ctl->rebuild, 1u);
-    }
+    finish_block(P, ctl, moved, false, true);
 }
 
 __global__ void k_signature(SimParams P, Ptrs D)
@@ -106,7 +99,7 @@ __global__ void k_signature(SimParams P, Ptrs D)
     const uint32_t par = D.ctl->parity;
     const uint32_t step = (uint32_t)D.ctl->step;
     float4 *vel = D.vel[par];
-    const uint32_t *tag = D.tag[par];
+    const uint32_t *tag = D.tag[D.ctl->oparity];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         float4 v = vel[i];
         v.w = __uint_as_float(signature(tag[i], step, P.key));
@@ -114,14 +107,152 @@ __global__ void k_signature(SimParams P, Ptrs D)
     }
 }
 
-// Pair force on particle i, one thread per particle over its full neighbour
-// row (every pair is evaluated by both of its particles, so no atomics and a
-// deterministic sum).  For each neighbour inside r_c (the FP32 predicate):
+// ---------------------------------------------------------------------------
+// Fused pair force.  Each warp owns 32 consecutive particles (cell order) and
+// walks their neighbour rows in lockstep, reading the k-th entry of all 32
+// rows in one coalesced load.  Pairs inside r_c (the FP32 predicate) are
+// appended to a per-warp ring queue in shared memory in (k, lane) order (a
+// ballot gives each hit its slot, as the paper's builder does for list
+// entries); every time 32 are queued the whole warp evaluates them together,
+// one pair per lane, so the hash / Box-Muller / force arithmetic runs with
+// full warps whatever the hit pattern.  The 32 results are summed per owning
+// particle in lane order (match-any groups, shuffles) and added to the
+// owner's shared accumulator: the summation order is fixed, the result
+// deterministic.  Every pair is evaluated for both of its particles (full
+// rows), so no thread writes another particle's force.
 //   F = a_{t_i t_j} w - gamma w_R^2 (e . v_ij) + sigma/sqrt(dt) w_R xi_ij,
 //   f_i += F e_ij,  e_ij = (x_i - x_j) / r.
-template <bool ONE_SPECIES, int SMODE>
-__global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, int out_fout, int inc_step)
+// The epilogue adds bonds and the body force and, per MODE, writes the force
+// or integrates (see launch_force).
+constexpr int kQueue = 64;  // ring slots per warp (< 32 pending + 32 new)
+
+// The candidate walk of a warp, templated on whether the minimum image can
+// be needed: a warp whose 32 particles all lie at least (r_list + skin) from
+// every face has no neighbour across the periodic boundary, so d = x_j - x_i
+// is already the minimum image and the pinned predicate reduces to it.
+template <bool WRAP>
+__device__ __forceinline__ float3 pair_delta(const SimParams &P, float4 pj, float4 pi)
 {
+    if (WRAP)
+        return make_float3(min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]), min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]),
+                           min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]));
+    return make_float3(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+}
+
+template <bool ONE_SPECIES, int SMODE, bool WRAP>
+__device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__restrict__ pos,
+                                           const float4 *__restrict__ vel, const uint32_t *__restrict__ row,
+                                           int cnt, int maxcnt, uint32_t self, float4 pi, int lane,
+                                           float4 (*s_q)[kQueue], uint8_t (*s_qo)[kQueue],
+                                           float4 (*s_vel)[32], float4 (*s_pos)[32], float (*s_acc)[3][32],
+                                           const float *a_tab, int warp)
+{
+    const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
+    // Evaluate queue entries [head, head + nb) (nb <= 32), one per lane, and
+    // add each owner's sum to its accumulator.
+    auto run_batch = [&](uint32_t head, int nb) {
+        float fx = 0.f, fy = 0.f, fz = 0.f;
+        uint32_t owner = 32u + (uint32_t)lane;  // distinct dummy owners for idle lanes
+        if (lane < nb) {
+            const uint32_t slot = (head + (uint32_t)lane) & (kQueue - 1);
+            const float4 q = s_q[warp][slot];  // (d, j)
+            const uint32_t qo = s_qo[warp][slot];
+            owner = qo & 31u;
+            const float4 wi = s_vel[warp][owner];
+            const float4 vj = __ldg(vel + __float_as_uint(q.w));
+            const float dx = q.x, dy = q.y, dz = q.z;
+            const float d2 = dist2_rn(dx, dy, dz);
+            const float inv_r = rsqrtf(d2);
+            const float r = d2 * inv_r;
+            const float w = fmaxf(fmaf(-r, P.inv_rc, 1.0f), 0.0f);
+            const float wR = weight_R<SMODE>(w, P.s);
+            // e_ij = -d / r; e . v_ij = -(d . (v_i - v_j)) / r
+            const float ev = -((dx * (wi.x - vj.x) + dy * (wi.y - vj.y)) + dz * (wi.z - vj.z)) * inv_r;
+            uint32_t A, B;
+            pair_hash(__float_as_uint(wi.w), __float_as_uint(vj.w), key, A, B);
+            const float xi = gauss_from_hash(A, B);
+            const float a = ONE_SPECIES ? P.a[0]
+                                        : a_tab[__float_as_int(s_pos[warp][owner].w) * P.n_species + (int)(qo >> 5)];
+            const float F = fmaf(a, w, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
+            const float sc = -F * inv_r;
+            fx = sc * dx;
+            fy = sc * dy;
+            fz = sc * dz;
+        }
+        // per-owner sums in lane order; the lowest lane of each group adds
+        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, owner);
+        const bool leader = (grp & lt_mask) == 0u;
+        int gmax = __popc(grp);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xFFFFFFFFu, gmax, o));
+        float sx = fx, sy = fy, sz = fz;
+        uint32_t rest = grp & (grp - 1u);  // group members after the lowest, in lane order
+        for (int t = 1; t < gmax; ++t) {
+            const int src = rest ? __ffs(rest) - 1 : lane;
+            const float ax = __shfl_sync(0xFFFFFFFFu, fx, src);
+            const float ay = __shfl_sync(0xFFFFFFFFu, fy, src);
+            const float az = __shfl_sync(0xFFFFFFFFu, fz, src);
+            if (rest) {
+                sx += ax;
+                sy += ay;
+                sz += az;
+            }
+            rest &= rest - 1u;
+        }
+        if (leader && owner < 32u) {
+            s_acc[warp][0][owner] += sx;
+            s_acc[warp][1][owner] += sy;
+            s_acc[warp][2][owner] += sz;
+        }
+        __syncwarp();
+    };
+
+    uint32_t head = 0u, tail = 0u;
+    // software pipeline: the row entry and position of candidate k+1 are
+    // loaded while candidate k is tested
+    uint32_t jc = self;
+    if (cnt > 0) jc = __ldg(row);
+    float4 pc = __ldg(pos + jc);
+    for (int k = 0; k < maxcnt; ++k) {
+        uint32_t jn = self;
+        if (k + 1 < cnt) jn = __ldg(row + (size_t)(k + 1) * 32);
+        const float4 pn = __ldg(pos + jn);
+        const float3 d = pair_delta<WRAP>(P, pc, pi);
+        const float d2 = dist2_rn(d.x, d.y, d.z);
+        const bool hit = k < cnt && d2 < P.rc2 && d2 > 0.0f;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+        if (hit) {
+            const uint32_t slot = (tail + (uint32_t)__popc(m & lt_mask)) & (kQueue - 1);
+            s_q[warp][slot] = make_float4(d.x, d.y, d.z, __uint_as_float(jc));
+            s_qo[warp][slot] = (uint8_t)((uint32_t)lane | (ONE_SPECIES ? 0u : ((uint32_t)__float_as_int(pc.w) << 5)));
+        }
+        tail += (uint32_t)__popc(m);
+        __syncwarp();
+        if (tail - head >= 32u) {
+            run_batch(head, 32);
+            head += 32u;
+        }
+        jc = jn;
+        pc = pn;
+    }
+    while (tail != head) {
+        const int nb = (int)min(32u, tail - head);
+        run_batch(head, nb);
+        head += (uint32_t)nb;
+    }
+}
+
+template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF>
+__global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, int out_fout)
+{
+    constexpr int W = kForceThreads / 32;
+    __shared__ float4 s_pos[W][32];
+    __shared__ float4 s_vel[W][32];
+    __shared__ float s_acc[W][3][32];
+    __shared__ float4 s_q[W][kQueue];
+    __shared__ uint8_t s_qo[W][kQueue];
     __shared__ float a_tab[kMaxSpecies * kMaxSpecies];
     if (!ONE_SPECIES) {
         for (int k = threadIdx.x; k < P.n_species * P.n_species; k += blockDim.x) a_tab[k] = P.a[k];
@@ -129,83 +260,109 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     }
     DevCtl *ctl = D.ctl;
     const uint32_t par = ctl->parity;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->rebuild = 0u;
-        if (inc_step) {
-            ctl->step += 1ull;
-            ctl->since_rebuild += 1u;
-        }
-    }
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
+    const uint32_t opar = ctl->oparity;
+    const unsigned long long step0 = ctl->step;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kForceThreads + threadIdx.x;
+    const bool valid = i < P.n;
     const float4 *__restrict__ pos = D.pos[par];
     const float4 *__restrict__ vel = D.vel[par];
-    const float4 pi = pos[i];
-    const float4 vi = vel[i];
-    const uint32_t si = __float_as_uint(vi.w);
-    const int ti = __float_as_int(pi.w);
-    const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
-    const float a0 = P.a[0];
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    const int cnt = (int)D.nnb[i];
+    const float4 pi = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 vi = valid ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    s_pos[warp][lane] = pi;
+    s_vel[warp][lane] = vi;
+    s_acc[warp][0][lane] = 0.f;
+    s_acc[warp][1][lane] = 0.f;
+    s_acc[warp][2][lane] = 0.f;
+    const int cnt = valid ? (int)D.nnb[i] : 0;
+    int maxcnt = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxcnt = max(maxcnt, __shfl_xor_sync(0xFFFFFFFFu, maxcnt, o));
     const uint32_t *__restrict__ row = D.nbr + (size_t)(i >> 5) * P.cap * 32 + (i & 31);
-    for (int k = 0; k < cnt; ++k) {
-        const uint32_t j = __ldg(row + (size_t)k * 32);
-        const float4 pj = __ldg(pos + j);
-        const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-        const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-        const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-        const float d2 = dist2_rn(dx, dy, dz);
-        if (d2 < P.rc2 && d2 > 0.0f) {
-            const float4 vj = __ldg(vel + j);
-            const float inv_r = rsqrtf(d2);
-            const float r = d2 * inv_r;
-            const float w = fmaxf(fmaf(-r, P.inv_rc, 1.0f), 0.0f);
-            const float wR = weight_R<SMODE>(w, P.s);
-            // e_ij = -d / r; e . v_ij = -(d . (v_i - v_j)) / r
-            const float ev = -((dx * (vi.x - vj.x) + dy * (vi.y - vj.y)) + dz * (vi.z - vj.z)) * inv_r;
-            uint32_t A, B;
-            pair_hash(si, __float_as_uint(vj.w), key, A, B);
-            const float xi = gauss_from_hash(A, B);
-            const float a = ONE_SPECIES ? a0 : a_tab[ti * P.n_species + __float_as_int(pj.w)];
-            const float F = fmaf(a, w, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
-            const float sc = -F * inv_r;
-            fx = fmaf(sc, dx, fx);
-            fy = fmaf(sc, dy, fy);
-            fz = fmaf(sc, dz, fz);
-        }
-    }
-    if (P.has_bonds) {
-        const uint32_t id = D.pid[par][i];
-        const uint32_t *bp = D.bond_partner + (size_t)id * kMaxBonds;
-        for (int b = 0; b < kMaxBonds; ++b) {
-            const uint32_t other = bp[b];
-            if (other == kNone) break;
-            const float4 pj = pos[D.idx_of_pid[other]];
-            const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-            const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-            const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 > 0.0f) {
-                const float inv_r = rsqrtf(d2);
-                const float r = d2 * inv_r;
-                // F_i = -K (r - r0) e_ij, e_ij = -d / r
-                const float sc = P.k_bond * (r - P.r0_bond) * inv_r;
-                fx = fmaf(sc, dx, fx);
-                fy = fmaf(sc, dy, fy);
-                fz = fmaf(sc, dz, fz);
+    const uint32_t self = valid ? (uint32_t)i : 0u;
+    // the warp may skip the minimum image when all its particles are far from the faces
+    const bool interior = !valid || (pi.x >= P.wrap_margin && pi.x <= P.L[0] - P.wrap_margin &&
+                                     pi.y >= P.wrap_margin && pi.y <= P.L[1] - P.wrap_margin &&
+                                     pi.z >= P.wrap_margin && pi.z <= P.L[2] - P.wrap_margin);
+    const bool all_interior = __all_sync(0xFFFFFFFFu, interior) && P.wrap_margin > 0.0f;
+    __syncwarp();
+    if (all_interior)
+        warp_pairs<ONE_SPECIES, SMODE, false>(P, pos, vel, row, cnt, maxcnt, self, pi, lane, s_q, s_qo, s_vel, s_pos,
+                                              s_acc, a_tab, warp);
+    else
+        warp_pairs<ONE_SPECIES, SMODE, true>(P, pos, vel, row, cnt, maxcnt, self, pi, lane, s_q, s_qo, s_vel, s_pos,
+                                             s_acc, a_tab, warp);
+    float fx = s_acc[warp][0][lane], fy = s_acc[warp][1][lane], fz = s_acc[warp][2][lane];
+
+    bool moved = false;
+    if (valid) {
+        if (P.has_bonds) {
+            const uint32_t id = D.pid[opar][i];
+            const uint32_t *bp = D.bond_partner + (size_t)id * kMaxBonds;
+            for (int b = 0; b < kMaxBonds; ++b) {
+                const uint32_t other = bp[b];
+                if (other == kNone) break;
+                const float4 pj = pos[D.idx_of_pid[other]];
+                const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+                const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+                const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 > 0.0f) {
+                    const float inv_r = rsqrtf(d2);
+                    const float r = d2 * inv_r;
+                    // F_i = -K (r - r0) e_ij, e_ij = -d / r
+                    const float sc = P.k_bond * (r - P.r0_bond) * inv_r;
+                    fx = fmaf(sc, dx, fx);
+                    fy = fmaf(sc, dy, fy);
+                    fz = fmaf(sc, dz, fz);
+                }
             }
         }
+        if (P.body_mode == 1) {
+            fx += P.body[0]; fy += P.body[1]; fz += P.body[2];
+        } else if (P.body_mode == 2) {
+            const float sg = pi.y < P.halfL[1] ? 1.0f : -1.0f;
+            fx = fmaf(sg, P.body[0], fx); fy = fmaf(sg, P.body[1], fy); fz = fmaf(sg, P.body[2], fz);
+        }
+        if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&ctl->err, kErrNonFinite);
+        const uint32_t nx = par ^ 1u;
+        if (MODE == kForceEval) {
+            float4 *out = out_fout ? D.fout : D.force[par];
+            out[i] = make_float4(fx, fy, fz, 0.0f);
+        } else if (MODE == kForceFinish) {
+            // phase 2: v = u + dt/2 f; the state at the full step goes to the other set
+            const float4 u = LHALF ? vi : D.vkick[par][i];
+            D.vel[nx][i] = make_float4(fmaf(P.half_dt, fx, u.x), fmaf(P.half_dt, fy, u.y), fmaf(P.half_dt, fz, u.z), vi.w);
+            D.pos[nx][i] = pi;
+            D.force[nx][i] = make_float4(fx, fy, fz, 0.0f);
+            if (!LHALF) D.vkick[nx][i] = u;
+        } else {
+            // phase 2 of this step and phase 1 of the next:
+            //   v = u + dt/2 f;  u' = v + dt/2 f;  v~ = v + lambda dt f;  x' = x + dt u'
+            const float4 u = LHALF ? vi : D.vkick[par][i];
+            float ux, uy, uz, tx, ty, tz;
+            if (LHALF) {
+                ux = fmaf(P.dt, fx, u.x); uy = fmaf(P.dt, fy, u.y); uz = fmaf(P.dt, fz, u.z);
+                tx = ux; ty = uy; tz = uz;
+            } else {
+                const float vx = fmaf(P.half_dt, fx, u.x), vy = fmaf(P.half_dt, fy, u.y), vz = fmaf(P.half_dt, fz, u.z);
+                ux = fmaf(P.half_dt, fx, vx); uy = fmaf(P.half_dt, fy, vy); uz = fmaf(P.half_dt, fz, vz);
+                tx = fmaf(P.lambda_dt, fx, vx); ty = fmaf(P.lambda_dt, fy, vy); tz = fmaf(P.lambda_dt, fz, vz);
+                D.vkick[nx][i] = make_float4(ux, uy, uz, 0.0f);
+            }
+            float4 x = pi;
+            x.x = wrap_pos(fmaf(P.dt, ux, x.x), P.L[0], 1.0f / P.L[0]);
+            x.y = wrap_pos(fmaf(P.dt, uy, x.y), P.L[1], 1.0f / P.L[1]);
+            x.z = wrap_pos(fmaf(P.dt, uz, x.z), P.L[2], 1.0f / P.L[2]);
+            D.pos[nx][i] = x;
+            const uint32_t sig = signature(D.tag[opar][i], (uint32_t)(step0 + 2ull), P.key);
+            D.vel[nx][i] = make_float4(tx, ty, tz, __uint_as_float(sig));
+            moved = moved_beyond(P, x, D.xref[i]);
+        }
     }
-    if (P.body_mode == 1) {
-        fx += P.body[0]; fy += P.body[1]; fz += P.body[2];
-    } else if (P.body_mode == 2) {
-        const float sg = pi.y < P.halfL[1] ? 1.0f : -1.0f;
-        fx = fmaf(sg, P.body[0], fx); fy = fmaf(sg, P.body[1], fy); fz = fmaf(sg, P.body[2], fz);
+    if (MODE != kForceEval) {
+        finish_block(P, ctl, moved, true, MODE == kForceStep);
     }
-    if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&ctl->err, kErrNonFinite);
-    float4 *out = out_fout ? D.fout : D.force[par];
-    out[i] = make_float4(fx, fy, fz, 0.0f);
 }
 
 // Deterministic block reduction of 8 doubles (fixed shuffle tree, then a
@@ -261,7 +418,7 @@ __global__ void __launch_bounds__(kThreads) k_observe(SimParams P, Ptrs D)
             }
         }
         if (P.has_bonds) {
-            const uint32_t *bp = D.bond_partner + (size_t)D.pid[par][i] * kMaxBonds;
+            const uint32_t *bp = D.bond_partner + (size_t)D.pid[D.ctl->oparity][i] * kMaxBonds;
             for (int b = 0; b < kMaxBonds && bp[b] != kNone; ++b) {
                 float4 pj = pos[D.idx_of_pid[bp[b]]];
                 float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
@@ -328,17 +485,29 @@ int grid_for(int n)
     return g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g);
 }
 
-template <bool ONE>
-cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int of, int inc, cudaStream_t s)
+template <bool ONE, int MODE, bool LH>
+cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream_t s)
 {
     const int g = (P.n + kForceThreads - 1) / kForceThreads;
     switch (P.s_mode) {
-    case 1: k_force<ONE, 1><<<g, kForceThreads, 0, s>>>(P, D, of, inc); break;
-    case 2: k_force<ONE, 2><<<g, kForceThreads, 0, s>>>(P, D, of, inc); break;
-    case 3: k_force<ONE, 3><<<g, kForceThreads, 0, s>>>(P, D, of, inc); break;
-    default: k_force<ONE, 0><<<g, kForceThreads, 0, s>>>(P, D, of, inc); break;
+    case 1: k_force<ONE, 1, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 2: k_force<ONE, 2, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 3: k_force<ONE, 3, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    default: k_force<ONE, 0, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
     }
     return cudaGetLastError();
+}
+
+template <bool ONE>
+cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, cudaStream_t s)
+{
+    if (mode == kForceEval) return launch_force_m<ONE, kForceEval, true>(P, D, of, s);
+    if (P.lambda_half) {
+        if (mode == kForceStep) return launch_force_m<ONE, kForceStep, true>(P, D, of, s);
+        return launch_force_m<ONE, kForceFinish, true>(P, D, of, s);
+    }
+    if (mode == kForceStep) return launch_force_m<ONE, kForceStep, false>(P, D, of, s);
+    return launch_force_m<ONE, kForceFinish, false>(P, D, of, s);
 }
 
 }  // namespace
@@ -351,25 +520,19 @@ cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_integrate(const SimParams &P, const Ptrs &D, int mode, cudaStream_t s)
+cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s)
 {
-    const int g = grid_for(P.n);
-    if (P.lambda_half) {
-        if (mode == 0) k_integrate<0, true><<<g, kThreads, 0, s>>>(P, D);
-        else if (mode == 1) k_integrate<1, true><<<g, kThreads, 0, s>>>(P, D);
-        else k_integrate<2, true><<<g, kThreads, 0, s>>>(P, D);
-    } else {
-        if (mode == 0) k_integrate<0, false><<<g, kThreads, 0, s>>>(P, D);
-        else if (mode == 1) k_integrate<1, false><<<g, kThreads, 0, s>>>(P, D);
-        else k_integrate<2, false><<<g, kThreads, 0, s>>>(P, D);
-    }
+    if (P.lambda_half)
+        k_phase1<true><<<grid_for(P.n), kThreads, 0, s>>>(P, D);
+    else
+        k_phase1<false><<<grid_for(P.n), kThreads, 0, s>>>(P, D);
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(const SimParams &P, const Ptrs &D, bool out_fout, bool inc_step, cudaStream_t s)
+cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s)
 {
-    if (P.n_species == 1) return launch_force_s<true>(P, D, out_fout ? 1 : 0, inc_step ? 1 : 0, s);
-    return launch_force_s<false>(P, D, out_fout ? 1 : 0, inc_step ? 1 : 0, s);
+    if (P.n_species == 1) return launch_force_s<true>(P, D, mode, out_fout ? 1 : 0, s);
+    return launch_force_s<false>(P, D, mode, out_fout ? 1 : 0, s);
 }
 
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s)

@@ -171,8 +171,7 @@ __global__ void k_scan_add(SimParams P, Ptrs D)
 __global__ void k_scatter(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
-    const uint32_t par = D.ctl->parity;
-    const uint32_t *pid = D.pid[par];
+    const uint32_t *pid = D.pid[D.ctl->oparity];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         uint32_t k = D.key[i];
         uint32_t dst = D.cell_start[k & kCellMask] + D.slot[i];
@@ -200,6 +199,7 @@ __global__ void k_gather(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
     const uint32_t s = D.ctl->parity, t = s ^ 1u;
+    const uint32_t os = D.ctl->oparity, ot = os ^ 1u;
     const int lim = P.n > P.ncell ? P.n : P.ncell;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lim; p += gridDim.x * blockDim.x) {
         if (p < P.n) {
@@ -210,9 +210,9 @@ __global__ void k_gather(SimParams P, Ptrs D)
             D.vel[t][p] = D.vel[s][i];
             if (!LHALF) D.vkick[t][p] = D.vkick[s][i];
             D.force[t][p] = D.force[s][i];
-            D.tag[t][p] = D.tag[s][i];
-            uint32_t id = D.pid[s][i];
-            D.pid[t][p] = id;
+            D.tag[ot][p] = D.tag[os][i];
+            uint32_t id = D.pid[os][i];
+            D.pid[ot][p] = id;
             D.idx_of_pid[id] = (uint32_t)p;
         }
         if (p < P.ncell) D.cell_count[p] = 0u;
@@ -224,6 +224,7 @@ __global__ void k_commit(Ptrs D)
     DevCtl *c = D.ctl;
     if (!c->rebuild) return;
     c->parity ^= 1u;
+    c->oparity ^= 1u;
     c->since_rebuild = 0u;
     c->nrebuild += 1ull;
     c->max_nnb = 0u;
@@ -269,6 +270,131 @@ __global__ void k_nbuild(SimParams P, Ptrs D)
     if ((threadIdx.x & 31) == 0) atomicMax(&D.ctl->max_nnb, local_max);
 }
 
+// Neighbour build staged through shared memory, one CTA per aligned brick of
+// kBrick^3 cells.  The CTA copies the positions of the brick's cells and of
+// the one-cell halo around it ((kBrick+2)^3 cells, each a contiguous range of
+// the cell-ordered arrays) into shared memory; then each thread takes one
+// particle of the brick and tests the particles of its 27 surrounding cells
+// from shared memory with the FP32 predicate, writing hits into its row in
+// the fixed stencil order (dz, dy, dx = -1..1): a deterministic row, built
+// without global gathers.  A brick whose halo holds more particles than the
+// shared buffer reads the overflow from global memory instead.
+constexpr int kBrick = 4;
+constexpr int kHalo = kBrick + 2;
+constexpr int kHaloCells = kHalo * kHalo * kHalo;  // 216
+constexpr int kBrickThreads = 256;
+constexpr int kBrickCap = 2816;                     // staged particles (44 KB)
+
+__global__ void __launch_bounds__(kBrickThreads) k_nbuild_brick(SimParams P, Ptrs D, int nbx, int nby)
+{
+    if (!D.ctl->rebuild) return;
+    __shared__ float4 s_pos[kBrickCap];
+    __shared__ uint32_t s_off[kHaloCells + 1];   // staged offset of each halo cell
+    __shared__ uint32_t s_gstart[kHaloCells];    // global start of each halo cell
+    __shared__ uint32_t s_cnt[kHaloCells];
+    __shared__ uint32_t s_wsum[kBrickThreads / 32];
+    __shared__ uint32_t s_lo, s_hi;
+    const uint32_t par = D.ctl->parity;
+    const float4 *pos = D.pos[par];
+    const int b = blockIdx.x;
+    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+    const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
+    if (threadIdx.x == 0) {
+        s_lo = 0xFFFFFFFFu;
+        s_hi = 0u;
+    }
+    __syncthreads();
+    // 1. halo cell ranges
+    uint32_t cnt = 0;
+    if (threadIdx.x < kHaloCells) {
+        const int t = threadIdx.x;
+        const int hx = t % kHalo, hy = (t / kHalo) % kHalo, hz = t / (kHalo * kHalo);
+        const int cx = (x0 + hx - 1 + P.nc[0]) % P.nc[0];
+        const int cy = (y0 + hy - 1 + P.nc[1]) % P.nc[1];
+        const int cz = (z0 + hz - 1 + P.nc[2]) % P.nc[2];
+        const uint32_t r = D.rank_of_cell[(cz * P.nc[1] + cy) * P.nc[0] + cx];
+        const uint32_t st = D.cell_start[r];
+        cnt = D.cell_start[r + 1] - st;
+        s_gstart[t] = st;
+        s_cnt[t] = cnt;
+        const bool inner = hx >= 1 && hx <= kBrick && hy >= 1 && hy <= kBrick && hz >= 1 && hz <= kBrick &&
+                           x0 + hx - 1 < P.nc[0] && y0 + hy - 1 < P.nc[1] && z0 + hz - 1 < P.nc[2];
+        if (inner) {
+            atomicMin(&s_lo, st);
+            atomicMax(&s_hi, st + cnt);
+        }
+    }
+    // block exclusive scan of the counts -> staged offsets
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_wsum[w];
+        if (threadIdx.x < kHaloCells) s_off[threadIdx.x] = before + incl - cnt;
+        if (threadIdx.x == kHaloCells - 1) s_off[kHaloCells] = before + incl;
+    }
+    __syncthreads();
+    // 2. stage positions: every thread copies elements e, e + blockDim, ... of
+    //    the concatenated halo ranges (its cell found by binary search over the
+    //    staged offsets), so all loads of a thread are independent
+    {
+        const uint32_t total = min(s_off[kHaloCells], (uint32_t)kBrickCap);
+        for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
+            int a = 0, bnd = kHaloCells;  // find c with s_off[c] <= e < s_off[c + 1]
+            while (bnd - a > 1) {
+                const int mid = (a + bnd) >> 1;
+                if (s_off[mid] <= e) a = mid; else bnd = mid;
+            }
+            s_pos[e] = pos[s_gstart[a] + (e - s_off[a])];
+        }
+    }
+    __syncthreads();
+    // 3. one thread per particle of the brick
+    const uint32_t lo = s_lo, hi = s_hi;
+    uint32_t local_max = 0;
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const float4 pi = pos[i];
+        float fx, fy, fz;
+        const int cx = cell_axis(pi.x, P.cells_per_len[0], P.nc[0], &fx);
+        const int cy = cell_axis(pi.y, P.cells_per_len[1], P.nc[1], &fy);
+        const int cz = cell_axis(pi.z, P.cells_per_len[2], P.nc[2], &fz);
+        const int hx = cx - x0 + 1, hy = cy - y0 + 1, hz = cz - z0 + 1;  // 1..kBrick
+        uint32_t *row = D.nbr + (size_t)(i >> 5) * P.cap * 32 + (i & 31);
+        uint32_t n_hit = 0;
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const int t = ((hz + oz) * kHalo + (hy + oy)) * kHalo + (hx + ox);
+                    const uint32_t o = s_off[t], n = s_cnt[t], st = s_gstart[t];
+                    for (uint32_t e = 0; e < n; ++e) {
+                        const uint32_t j = st + e;
+                        const float4 pj = (o + e < (uint32_t)kBrickCap) ? s_pos[o + e] : pos[j];
+                        const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+                        const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+                        const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+                        if (dist2_rn(dx, dy, dz) < P.rlist2 && j != i) {
+                            if (n_hit < (uint32_t)P.cap) row[(size_t)n_hit * 32] = j;
+                            ++n_hit;
+                        }
+                    }
+                }
+        if (n_hit > (uint32_t)P.cap) atomicOr(&D.ctl->err, kErrNbrOverflow);
+        D.nnb[i] = n_hit < (uint32_t)P.cap ? n_hit : (uint32_t)P.cap;
+        local_max = n_hit > local_max ? n_hit : local_max;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, local_max, o);
+        local_max = y > local_max ? y : local_max;
+    }
+    if ((threadIdx.x & 31) == 0 && local_max) atomicMax(&D.ctl->max_nnb, local_max);
+}
+
 }  // namespace
 
 int scan_blocks_for(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
@@ -288,7 +414,13 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
     else
         k_gather<false><<<gg, kThreads, 0, s>>>(P, D);
     k_commit<<<1, 1, 0, s>>>(D);
-    k_nbuild<<<g, kThreads, 0, s>>>(P, D);
+    if (P.nc[0] >= 3 && P.nc[1] >= 3 && P.nc[2] >= 3) {
+        const int nbx = (P.nc[0] + kBrick - 1) / kBrick, nby = (P.nc[1] + kBrick - 1) / kBrick;
+        const int nbz = (P.nc[2] + kBrick - 1) / kBrick;
+        k_nbuild_brick<<<nbx * nby * nbz, kBrickThreads, 0, s>>>(P, D, nbx, nby);
+    } else {
+        k_nbuild<<<g, kThreads, 0, s>>>(P, D);
+    }
     return cudaGetLastError();
 }
 
