@@ -27,10 +27,16 @@ constexpr int kMaxSpecies = 8;
 constexpr int kMaxBonds = 6;          // bonds per particle
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kStencil = 27;
+// bricks: aligned kBrick^3 blocks of cells (contiguous ranges of the Morton
+// cell order) with a one-cell halo, staged in shared memory by the builder
+constexpr int kBrick = 4;
+constexpr int kHalo = kBrick + 2;
+constexpr int kHaloCells = kHalo * kHalo * kHalo;  // 216
 
 // device error bits
 constexpr uint32_t kErrNbrOverflow = 1u;
 constexpr uint32_t kErrNonFinite = 2u;
+constexpr uint32_t kErrTimeout = 4u;  // a bounded device-side wait ran out
 
 struct DevCtl {
     uint32_t parity;         // live set of the state arrays (pos, vel, vkick, force)
@@ -71,6 +77,10 @@ struct SimParams {
     float a[kMaxSpecies * kMaxSpecies];
     float k_bond, r0_bond;
     int has_bonds;
+    int use_bricks;           // every axis has >= 3 cells: brick kernels, brick-local rows
+    int brick_cap;            // halo particles the brick builder stages in shared memory
+    int nb[3];                // bricks per axis
+    int nbricks;
 };
 
 struct Ptrs {
@@ -94,6 +104,9 @@ struct Ptrs {
     // neighbours
     uint32_t *nbr;                 // tiled list
     uint32_t *nnb;                 // [n] counts
+    // bricks
+    const uint32_t *brick_rank_lo; // [nbricks] first Morton rank of the brick's cells
+    const uint32_t *brick_rank_hi; // [nbricks] last Morton rank (inclusive)
     // bonds
     const uint32_t *bond_partner;  // [n][kMaxBonds] partner caller indices
     // reductions
@@ -121,6 +134,10 @@ cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int 
 cudaError_t launch_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *ti, const uint32_t *tj,
                             uint32_t *out_hash, float *out_xi, cudaStream_t s);
 int scan_blocks_for(int ncell);
+// one-time kernel attributes (dynamic shared memory of the brick kernels)
+cudaError_t init_kernel_attributes();
+// largest brick_cap the builder's shared-memory limit allows
+int max_brick_cap();
 int observe_blocks_for(int n);
 
 }  // namespace dpd

@@ -32,6 +32,8 @@ struct Geometry {
     int ncell;
     std::vector<uint32_t> rank_of_cell;  // linear (cz, cy, cx) -> rank
     std::vector<uint32_t> stencil;       // [ncell][27]
+    int nb[3] = {0, 0, 0};               // bricks per axis
+    std::vector<uint32_t> brick_lo, brick_hi;  // first / last Morton rank of each brick
 };
 
 uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
@@ -87,6 +89,19 @@ void build_geometry(const int nc[3], Geometry &g)
         std::sort(tmp.begin(), tmp.end());
         std::copy(tmp.begin(), tmp.end(), g.stencil.begin() + (size_t)r * kStencil);
     }
+    // aligned kBrick^3 blocks of cells: consecutive Morton ranks
+    for (int a = 0; a < 3; ++a) g.nb[a] = (nc[a] + kBrick - 1) / kBrick;
+    const int nbricks = g.nb[0] * g.nb[1] * g.nb[2];
+    g.brick_lo.assign(nbricks, 0xFFFFFFFFu);
+    g.brick_hi.assign(nbricks, 0u);
+    for (int z = 0; z < nc[2]; ++z)
+        for (int y = 0; y < nc[1]; ++y)
+            for (int x = 0; x < nc[0]; ++x) {
+                const int b = ((z / kBrick) * g.nb[1] + y / kBrick) * g.nb[0] + x / kBrick;
+                const uint32_t r = g.rank_of_cell[(z * nc[1] + y) * nc[0] + x];
+                g.brick_lo[b] = std::min(g.brick_lo[b], r);
+                g.brick_hi[b] = std::max(g.brick_hi[b], r);
+            }
 }
 
 }  // namespace
@@ -191,6 +206,7 @@ dpd_status check_err(dpd_sim *h, DevCtl &c)
         return fail(h, DPD_ERR_NBR_OVERFLOW,
                     "neighbour list overflow: " + std::to_string(c.max_nnb) + " > capacity " + std::to_string(h->P.cap));
     if (c.err & kErrNonFinite) return fail(h, DPD_ERR_NONFINITE, "non-finite force");
+    if (c.err & kErrTimeout) return fail(h, DPD_ERR_TIMEOUT, "a device-side wait for staged data ran out");
     return DPD_OK;
 }
 
@@ -202,7 +218,7 @@ void drop_graphs(dpd_sim *h)
     h->timed_graphs.clear();
 }
 
-constexpr int kRebuildKernels = 9;  // bin, 3 scan, scatter, rank, gather, commit, nbuild
+constexpr int kRebuildKernels = 9;  // bin, 3 scan, scatter, rank, gather, commit, nbuild (+ brick tiles)
 
 // Timing event on the stream; inside a graph capture it becomes an event
 // record node whose timestamp stays readable after the graph runs.
@@ -268,6 +284,9 @@ dpd_status get_graph(dpd_sim *h, int k, cudaGraphExec_t *out)
     return DPD_OK;
 }
 
+// Row tiles of 32 consecutive particles.
+size_t row_tiles(const dpd_sim *, int64_t n) { return (size_t)(n + 31) / 32; }
+
 int auto_capacity(const dpd_sim *h, int64_t n)
 {
     double V = h->box[0] * h->box[1] * h->box[2];
@@ -304,8 +323,7 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     A((void **)&D.perm, u4);
     A((void **)&D.idx_of_pid, u4);
     A((void **)&D.nnb, u4);
-    const size_t tiles = (size_t)(n + 31) / 32;
-    A((void **)&D.nbr, tiles * 32 * (size_t)cap * sizeof(uint32_t));
+    A((void **)&D.nbr, row_tiles(h, n) * 32 * (size_t)cap * sizeof(uint32_t));
     h->red_doubles = std::max<size_t>((size_t)observe_blocks_for((int)n) * 8, 4096);
     A((void **)&D.red, h->red_doubles * sizeof(double));
     A((void **)&D.bond_partner, sizeof(uint32_t) * (size_t)n * kMaxBonds);
@@ -333,7 +351,7 @@ dpd_status rebuild_and_force(dpd_sim *h, bool grow_on_overflow)
         int cap = (int)((c.max_nnb * 5 / 4 + 16 + 7) / 8 * 8);
         cudaFree(h->D.nbr);
         h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->D.nbr));
-        st = dev_alloc(h, (void **)&h->D.nbr, (size_t)(h->n + 31) / 32 * 32 * (size_t)cap * sizeof(uint32_t), h->allocs);
+        st = dev_alloc(h, (void **)&h->D.nbr, row_tiles(h, h->n) * 32 * (size_t)cap * sizeof(uint32_t), h->allocs);
         if (st) return st;
         h->P.cap = cap;
         drop_graphs(h);
@@ -487,6 +505,14 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     }
     build_geometry(nc, h->geo);
     h->n_scan_blocks = scan_blocks_for(P.ncell);
+    P.use_bricks = (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3) ? 1 : 0;
+    for (int a = 0; a < 3; ++a) P.nb[a] = h->geo.nb[a];
+    P.nbricks = h->geo.nb[0] * h->geo.nb[1] * h->geo.nb[2];
+    if (cudaError_t ea = init_kernel_attributes(); ea != cudaSuccess) {
+        cudaGetLastError();
+        dpd_destroy(h);
+        return fail(nullptr, DPD_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(ea));
+    }
     dpd_status st = DPD_OK;
     auto A = [&](void **p, size_t b) { if (st == DPD_OK) st = dev_alloc(h, p, b, h->static_allocs); };
     A((void **)&h->D.ctl, sizeof(DevCtl));
@@ -495,6 +521,9 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     A((void **)&h->D.cell_count, sizeof(uint32_t) * P.ncell);
     A((void **)&h->D.cell_start, sizeof(uint32_t) * (P.ncell + 1));
     A((void **)&h->D.scan_part, sizeof(uint32_t) * (h->n_scan_blocks + 1));
+    A((void **)&h->D.brick_rank_lo, sizeof(uint32_t) * P.nbricks);
+    A((void **)&h->D.brick_rank_hi, sizeof(uint32_t) * P.nbricks);
+
     if (st) {
         std::string m = h->err;
         dpd_destroy(h);
@@ -504,6 +533,12 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
                                     cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync((void *)h->D.stencil, h->geo.stencil.data(), sizeof(uint32_t) * (size_t)P.ncell * kStencil,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)h->D.brick_rank_lo, h->geo.brick_lo.data(), sizeof(uint32_t) * P.nbricks,
+                            cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)h->D.brick_rank_hi, h->geo.brick_hi.data(), sizeof(uint32_t) * P.nbricks,
                             cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->D.cell_count, 0, sizeof(uint32_t) * P.ncell, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->D.ctl, 0, sizeof(DevCtl), h->stream);
@@ -550,6 +585,15 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
         if (std::adjacent_find(s.begin(), s.end()) != s.end()) return fail(h, DPD_ERR_ARG, "tags must be distinct");
     }
     int cap = h->opt.nbr_capacity > 0 ? h->opt.nbr_capacity : auto_capacity(h, n);
+    if (h->P.use_bricks) {
+        // staging buffer of the brick builder: the expected halo population
+        // with a wide margin; a brick beyond it reads global memory
+        const double cellvol = (h->box[0] / h->P.nc[0]) * (h->box[1] / h->P.nc[1]) * (h->box[2] / h->P.nc[2]);
+        const double mean = (double)n / (h->box[0] * h->box[1] * h->box[2]) * cellvol * kHaloCells;
+        int bc = (int)std::ceil(1.1 * mean + 6.0 * std::sqrt(mean) + 64.0);
+        bc = (bc + 31) / 32 * 32;
+        h->P.brick_cap = std::min(std::max(bc, 256), std::min(max_brick_cap(), 65535));
+    }
     if (n != h->n || cap != h->P.cap || h->cap_alloc_n != n) {
         h->n = n;
         h->P.n = (int)n;
@@ -626,7 +670,7 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
     st = read_ctl(h, c);
     if (st) return st;
     const int64_t n = h->n;
-    const size_t tiles = (size_t)(n + 31) / 32;
+    const size_t tiles = row_tiles(h, n);
     std::vector<uint32_t> nbr(tiles * 32 * (size_t)h->P.cap), nnb(n), pid(n);
     CUDA_TRY(h, cudaMemcpyAsync(nbr.data(), h->D.nbr, sizeof(uint32_t) * nbr.size(), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(nnb.data(), h->D.nnb, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
@@ -637,10 +681,10 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
     for (int64_t i = 0; i < n; ++i) {
         const uint32_t *row = nbr.data() + (size_t)(i >> 5) * h->P.cap * 32 + (i & 31);
         for (uint32_t k = 0; k < nnb[i]; ++k) {
-            uint32_t j = row[(size_t)k * 32];
+            const uint32_t j = row[(size_t)k * 32];
             if (j >= (uint32_t)n) return fail(h, DPD_ERR_STATE, "neighbour index out of range");
-            uint32_t a = pid[i], b = pid[j];
-            if (a < b) pr.push_back(((uint64_t)a << 32) | b);
+            const uint32_t a = pid[i], b2 = pid[j];
+            if (a < b2) pr.push_back(((uint64_t)a << 32) | b2);
         }
     }
     std::sort(pr.begin(), pr.end());
@@ -779,7 +823,7 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
         }
         out->steps = nsteps;
         out->force_launches = nsteps;
-        out->kernel_launches = nsteps * (1 + kRebuildKernels) + 1;
+        out->kernel_launches = nsteps * (1 + kRebuildKernels + (h->P.use_bricks ? 1 : 0)) + 1;
         out->rebuilds = (int64_t)(c.nrebuild - c0.nrebuild);
     }
     return DPD_OK;

@@ -107,6 +107,82 @@ __global__ void k_signature(SimParams P, Ptrs D)
     }
 }
 
+// Epilogue of the force kernels for particle i: bonds, body force, then per
+// MODE the force is stored, or the step is integrated into the other buffer
+// set.  Returns whether the particle moved past the rebuild threshold.
+template <int MODE, bool LHALF>
+__device__ __forceinline__ bool force_epilogue(const SimParams &P, const Ptrs &D, DevCtl *ctl, int i, float4 pi,
+                                               float4 vi, float fx, float fy, float fz, uint32_t par, uint32_t opar,
+                                               unsigned long long step0, int out_fout)
+{
+    bool moved = false;
+    const float4 *__restrict__ pos = D.pos[par];
+    if (P.has_bonds) {
+        const uint32_t id = D.pid[opar][i];
+        const uint32_t *bp = D.bond_partner + (size_t)id * kMaxBonds;
+        for (int b = 0; b < kMaxBonds; ++b) {
+            const uint32_t other = bp[b];
+            if (other == kNone) break;
+            const float4 pj = pos[D.idx_of_pid[other]];
+            const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+            const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+            const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 > 0.0f) {
+                const float inv_r = rsqrtf(d2);
+                const float r = d2 * inv_r;
+                // F_i = -K (r - r0) e_ij, e_ij = -d / r
+                const float sc = P.k_bond * (r - P.r0_bond) * inv_r;
+                fx = fmaf(sc, dx, fx);
+                fy = fmaf(sc, dy, fy);
+                fz = fmaf(sc, dz, fz);
+            }
+        }
+    }
+    if (P.body_mode == 1) {
+        fx += P.body[0]; fy += P.body[1]; fz += P.body[2];
+    } else if (P.body_mode == 2) {
+        const float sg = pi.y < P.halfL[1] ? 1.0f : -1.0f;
+        fx = fmaf(sg, P.body[0], fx); fy = fmaf(sg, P.body[1], fy); fz = fmaf(sg, P.body[2], fz);
+    }
+    if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&ctl->err, kErrNonFinite);
+    const uint32_t nx = par ^ 1u;
+    if (MODE == kForceEval) {
+        float4 *out = out_fout ? D.fout : D.force[par];
+        out[i] = make_float4(fx, fy, fz, 0.0f);
+    } else if (MODE == kForceFinish) {
+        // phase 2: v = u + dt/2 f; the state at the full step goes to the other set
+        const float4 u = LHALF ? vi : D.vkick[par][i];
+        D.vel[nx][i] = make_float4(fmaf(P.half_dt, fx, u.x), fmaf(P.half_dt, fy, u.y), fmaf(P.half_dt, fz, u.z), vi.w);
+        D.pos[nx][i] = pi;
+        D.force[nx][i] = make_float4(fx, fy, fz, 0.0f);
+        if (!LHALF) D.vkick[nx][i] = u;
+    } else {
+        // phase 2 of this step and phase 1 of the next:
+        //   v = u + dt/2 f;  u' = v + dt/2 f;  v~ = v + lambda dt f;  x' = x + dt u'
+        const float4 u = LHALF ? vi : D.vkick[par][i];
+        float ux, uy, uz, tx, ty, tz;
+        if (LHALF) {
+            ux = fmaf(P.dt, fx, u.x); uy = fmaf(P.dt, fy, u.y); uz = fmaf(P.dt, fz, u.z);
+            tx = ux; ty = uy; tz = uz;
+        } else {
+            const float vx = fmaf(P.half_dt, fx, u.x), vy = fmaf(P.half_dt, fy, u.y), vz = fmaf(P.half_dt, fz, u.z);
+            ux = fmaf(P.half_dt, fx, vx); uy = fmaf(P.half_dt, fy, vy); uz = fmaf(P.half_dt, fz, vz);
+            tx = fmaf(P.lambda_dt, fx, vx); ty = fmaf(P.lambda_dt, fy, vy); tz = fmaf(P.lambda_dt, fz, vz);
+            D.vkick[nx][i] = make_float4(ux, uy, uz, 0.0f);
+        }
+        float4 x = pi;
+        x.x = wrap_pos(fmaf(P.dt, ux, x.x), P.L[0], 1.0f / P.L[0]);
+        x.y = wrap_pos(fmaf(P.dt, uy, x.y), P.L[1], 1.0f / P.L[1]);
+        x.z = wrap_pos(fmaf(P.dt, uz, x.z), P.L[2], 1.0f / P.L[2]);
+        D.pos[nx][i] = x;
+        const uint32_t sig = signature(D.tag[opar][i], (uint32_t)(step0 + 2ull), P.key);
+        D.vel[nx][i] = make_float4(tx, ty, tz, __uint_as_float(sig));
+        moved = moved_beyond(P, x, D.xref[i]);
+    }
+    return moved;
+}
+
 // ---------------------------------------------------------------------------
 // Fused pair force.  Each warp owns 32 consecutive particles (cell order) and
 // walks their neighbour rows in lockstep, reading the k-th entry of all 32
@@ -142,10 +218,9 @@ __device__ __forceinline__ float3 pair_delta(const SimParams &P, float4 pj, floa
 template <bool ONE_SPECIES, int SMODE, bool WRAP>
 __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__restrict__ pos,
                                            const float4 *__restrict__ vel, const uint32_t *__restrict__ row,
-                                           int cnt, int maxcnt, uint32_t self, float4 pi, int lane,
-                                           float4 (*s_q)[kQueue], uint8_t (*s_qo)[kQueue],
-                                           float4 (*s_vel)[32], float4 (*s_pos)[32], float (*s_acc)[3][32],
-                                           const float *a_tab, int warp)
+                                           int cnt, int maxcnt, uint32_t self, uint32_t own_idx, float4 pi,
+                                           int lane, float4 (*s_q)[kQueue], uint8_t (*s_qo)[kQueue],
+                                           float (*s_acc)[3][32], const float *a_tab, int warp)
 {
     const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -154,13 +229,20 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
     // add each owner's sum to its accumulator.
     auto run_batch = [&](uint32_t head, int nb) {
         float fx = 0.f, fy = 0.f, fz = 0.f;
-        uint32_t owner = 32u + (uint32_t)lane;  // distinct dummy owners for idle lanes
-        if (lane < nb) {
+        const bool act = lane < nb;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t qo = (uint32_t)lane;
+        if (act) {
             const uint32_t slot = (head + (uint32_t)lane) & (kQueue - 1);
-            const float4 q = s_q[warp][slot];  // (d, j)
-            const uint32_t qo = s_qo[warp][slot];
+            q = s_q[warp][slot];  // (d, j)
+            qo = s_qo[warp][slot];
+        }
+        // the owning particle's data, at its index held by the owner lane
+        const uint32_t oidx = __shfl_sync(0xFFFFFFFFu, own_idx, (int)(qo & 31u));
+        uint32_t owner = 32u + (uint32_t)lane;  // distinct dummy owners for idle lanes
+        if (act) {
             owner = qo & 31u;
-            const float4 wi = s_vel[warp][owner];
+            const float4 wi = __ldg(vel + oidx);
             const float4 vj = __ldg(vel + __float_as_uint(q.w));
             const float dx = q.x, dy = q.y, dz = q.z;
             const float d2 = dist2_rn(dx, dy, dz);
@@ -174,7 +256,7 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             pair_hash(__float_as_uint(wi.w), __float_as_uint(vj.w), key, A, B);
             const float xi = gauss_from_hash(A, B);
             const float a = ONE_SPECIES ? P.a[0]
-                                        : a_tab[__float_as_int(s_pos[warp][owner].w) * P.n_species + (int)(qo >> 5)];
+                                        : a_tab[__float_as_int(__ldg(pos + oidx).w) * P.n_species + (int)(qo >> 5)];
             const float F = fmaf(a, w, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
             const float sc = -F * inv_r;
             fx = sc * dx;
@@ -210,23 +292,17 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
     };
 
     uint32_t head = 0u, tail = 0u;
-    // software pipeline: the row entry and position of candidate k+1 are
-    // loaded while candidate k is tested
-    uint32_t jc = self;
-    if (cnt > 0) jc = __ldg(row);
-    float4 pc = __ldg(pos + jc);
-    for (int k = 0; k < maxcnt; ++k) {
-        uint32_t jn = self;
-        if (k + 1 < cnt) jn = __ldg(row + (size_t)(k + 1) * 32);
-        const float4 pn = __ldg(pos + jn);
-        const float3 d = pair_delta<WRAP>(P, pc, pi);
+    // one candidate: test it, queue it if inside r_c, evaluate a full batch
+    auto candidate = [&](int k, uint32_t j, float4 pj) {
+        const float3 d = pair_delta<WRAP>(P, pj, pi);
         const float d2 = dist2_rn(d.x, d.y, d.z);
-        const bool hit = k < cnt && d2 < P.rc2 && d2 > 0.0f;
+        // bitwise & keeps the test branch-free (no short-circuit evaluation)
+        const bool hit = (k < cnt) & (d2 < P.rc2) & (d2 > 0.0f);
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
         if (hit) {
             const uint32_t slot = (tail + (uint32_t)__popc(m & lt_mask)) & (kQueue - 1);
-            s_q[warp][slot] = make_float4(d.x, d.y, d.z, __uint_as_float(jc));
-            s_qo[warp][slot] = (uint8_t)((uint32_t)lane | (ONE_SPECIES ? 0u : ((uint32_t)__float_as_int(pc.w) << 5)));
+            s_q[warp][slot] = make_float4(d.x, d.y, d.z, __uint_as_float(j));
+            s_qo[warp][slot] = (uint8_t)((uint32_t)lane | (ONE_SPECIES ? 0u : ((uint32_t)__float_as_int(pj.w) << 5)));
         }
         tail += (uint32_t)__popc(m);
         __syncwarp();
@@ -234,6 +310,17 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             run_batch(head, 32);
             head += 32u;
         }
+    };
+    // 32-bit rows, entry k at k * 32: the row entry and position of
+    // candidate k+1 are loaded while candidate k is tested
+    uint32_t jc = self;
+    if (cnt > 0) jc = __ldg(row + lane);
+    float4 pc = __ldg(pos + jc);
+    for (int k = 0; k < maxcnt; ++k) {
+        uint32_t jn = self;
+        if (k + 1 < cnt) jn = __ldg(row + (size_t)(k + 1) * 32 + lane);
+        const float4 pn = __ldg(pos + jn);
+        candidate(k, jc, pc);
         jc = jn;
         pc = pn;
     }
@@ -248,8 +335,6 @@ template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF>
 __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, int out_fout)
 {
     constexpr int W = kForceThreads / 32;
-    __shared__ float4 s_pos[W][32];
-    __shared__ float4 s_vel[W][32];
     __shared__ float s_acc[W][3][32];
     __shared__ float4 s_q[W][kQueue];
     __shared__ uint8_t s_qo[W][kQueue];
@@ -269,8 +354,6 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     const float4 *__restrict__ vel = D.vel[par];
     const float4 pi = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 vi = valid ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    s_pos[warp][lane] = pi;
-    s_vel[warp][lane] = vi;
     s_acc[warp][0][lane] = 0.f;
     s_acc[warp][1][lane] = 0.f;
     s_acc[warp][2][lane] = 0.f;
@@ -278,7 +361,7 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     int maxcnt = cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxcnt = max(maxcnt, __shfl_xor_sync(0xFFFFFFFFu, maxcnt, o));
-    const uint32_t *__restrict__ row = D.nbr + (size_t)(i >> 5) * P.cap * 32 + (i & 31);
+    const uint32_t *__restrict__ row = D.nbr + (size_t)(i >> 5) * P.cap * 32;  // tile of the warp
     const uint32_t self = valid ? (uint32_t)i : 0u;
     // the warp may skip the minimum image when all its particles are far from the faces
     const bool interior = !valid || (pi.x >= P.wrap_margin && pi.x <= P.L[0] - P.wrap_margin &&
@@ -287,83 +370,21 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     const bool all_interior = __all_sync(0xFFFFFFFFu, interior) && P.wrap_margin > 0.0f;
     __syncwarp();
     if (all_interior)
-        warp_pairs<ONE_SPECIES, SMODE, false>(P, pos, vel, row, cnt, maxcnt, self, pi, lane, s_q, s_qo, s_vel, s_pos,
-                                              s_acc, a_tab, warp);
+        warp_pairs<ONE_SPECIES, SMODE, false>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
+                                                     s_acc, a_tab, warp);
     else
-        warp_pairs<ONE_SPECIES, SMODE, true>(P, pos, vel, row, cnt, maxcnt, self, pi, lane, s_q, s_qo, s_vel, s_pos,
-                                             s_acc, a_tab, warp);
+        warp_pairs<ONE_SPECIES, SMODE, true>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
+                                                    s_acc, a_tab, warp);
     float fx = s_acc[warp][0][lane], fy = s_acc[warp][1][lane], fz = s_acc[warp][2][lane];
 
     bool moved = false;
-    if (valid) {
-        if (P.has_bonds) {
-            const uint32_t id = D.pid[opar][i];
-            const uint32_t *bp = D.bond_partner + (size_t)id * kMaxBonds;
-            for (int b = 0; b < kMaxBonds; ++b) {
-                const uint32_t other = bp[b];
-                if (other == kNone) break;
-                const float4 pj = pos[D.idx_of_pid[other]];
-                const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-                const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-                const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-                const float d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 > 0.0f) {
-                    const float inv_r = rsqrtf(d2);
-                    const float r = d2 * inv_r;
-                    // F_i = -K (r - r0) e_ij, e_ij = -d / r
-                    const float sc = P.k_bond * (r - P.r0_bond) * inv_r;
-                    fx = fmaf(sc, dx, fx);
-                    fy = fmaf(sc, dy, fy);
-                    fz = fmaf(sc, dz, fz);
-                }
-            }
-        }
-        if (P.body_mode == 1) {
-            fx += P.body[0]; fy += P.body[1]; fz += P.body[2];
-        } else if (P.body_mode == 2) {
-            const float sg = pi.y < P.halfL[1] ? 1.0f : -1.0f;
-            fx = fmaf(sg, P.body[0], fx); fy = fmaf(sg, P.body[1], fy); fz = fmaf(sg, P.body[2], fz);
-        }
-        if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&ctl->err, kErrNonFinite);
-        const uint32_t nx = par ^ 1u;
-        if (MODE == kForceEval) {
-            float4 *out = out_fout ? D.fout : D.force[par];
-            out[i] = make_float4(fx, fy, fz, 0.0f);
-        } else if (MODE == kForceFinish) {
-            // phase 2: v = u + dt/2 f; the state at the full step goes to the other set
-            const float4 u = LHALF ? vi : D.vkick[par][i];
-            D.vel[nx][i] = make_float4(fmaf(P.half_dt, fx, u.x), fmaf(P.half_dt, fy, u.y), fmaf(P.half_dt, fz, u.z), vi.w);
-            D.pos[nx][i] = pi;
-            D.force[nx][i] = make_float4(fx, fy, fz, 0.0f);
-            if (!LHALF) D.vkick[nx][i] = u;
-        } else {
-            // phase 2 of this step and phase 1 of the next:
-            //   v = u + dt/2 f;  u' = v + dt/2 f;  v~ = v + lambda dt f;  x' = x + dt u'
-            const float4 u = LHALF ? vi : D.vkick[par][i];
-            float ux, uy, uz, tx, ty, tz;
-            if (LHALF) {
-                ux = fmaf(P.dt, fx, u.x); uy = fmaf(P.dt, fy, u.y); uz = fmaf(P.dt, fz, u.z);
-                tx = ux; ty = uy; tz = uz;
-            } else {
-                const float vx = fmaf(P.half_dt, fx, u.x), vy = fmaf(P.half_dt, fy, u.y), vz = fmaf(P.half_dt, fz, u.z);
-                ux = fmaf(P.half_dt, fx, vx); uy = fmaf(P.half_dt, fy, vy); uz = fmaf(P.half_dt, fz, vz);
-                tx = fmaf(P.lambda_dt, fx, vx); ty = fmaf(P.lambda_dt, fy, vy); tz = fmaf(P.lambda_dt, fz, vz);
-                D.vkick[nx][i] = make_float4(ux, uy, uz, 0.0f);
-            }
-            float4 x = pi;
-            x.x = wrap_pos(fmaf(P.dt, ux, x.x), P.L[0], 1.0f / P.L[0]);
-            x.y = wrap_pos(fmaf(P.dt, uy, x.y), P.L[1], 1.0f / P.L[1]);
-            x.z = wrap_pos(fmaf(P.dt, uz, x.z), P.L[2], 1.0f / P.L[2]);
-            D.pos[nx][i] = x;
-            const uint32_t sig = signature(D.tag[opar][i], (uint32_t)(step0 + 2ull), P.key);
-            D.vel[nx][i] = make_float4(tx, ty, tz, __uint_as_float(sig));
-            moved = moved_beyond(P, x, D.xref[i]);
-        }
-    }
+    if (valid)
+        moved = force_epilogue<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout);
     if (MODE != kForceEval) {
         finish_block(P, ctl, moved, true, MODE == kForceStep);
     }
 }
+
 
 // Deterministic block reduction of 8 doubles (fixed shuffle tree, then a
 // fixed order over the warps); thread 0 writes the block's partials.
@@ -401,20 +422,30 @@ __global__ void __launch_bounds__(kThreads) k_observe(SimParams P, Ptrs D)
         acc[1] = v.x; acc[2] = v.y; acc[3] = v.z;
         float4 pi = pos[i];
         const int ti = __float_as_int(pi.w);
-        const int cnt = (int)D.nnb[i];
-        const uint32_t *row = D.nbr + (size_t)(i >> 5) * P.cap * 32 + (i & 31);
+        // pairs inside r_c from the cell list (27 surrounding cells of the
+        // last build; cells are at least r_list wide and no particle has
+        // moved more than skin/2 since), independent of the row format
+        const int cx = min(max((int)(pi.x * P.cells_per_len[0]), 0), P.nc[0] - 1);
+        const int cy = min(max((int)(pi.y * P.cells_per_len[1]), 0), P.nc[1] - 1);
+        const int cz = min(max((int)(pi.z * P.cells_per_len[2]), 0), P.nc[2] - 1);
+        const uint32_t c = D.rank_of_cell[(cz * P.nc[1] + cy) * P.nc[0] + cx];
         double vir = 0.0;
-        for (int k = 0; k < cnt; ++k) {
-            float4 pj = pos[row[(size_t)k * 32]];
-            float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-            float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-            float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-            float d2 = dist2_rn(dx, dy, dz);
-            if (d2 < P.rc2 && d2 > 0.0f) {
-                float r = sqrtf(d2);
-                float w = fmaxf(1.0f - r * P.inv_rc, 0.0f);
-                float a = ONE_SPECIES ? P.a[0] : P.a[ti * P.n_species + __float_as_int(pj.w)];
-                vir += 0.5 * (double)(a * w * r);
+        for (int sidx = 0; sidx < kStencil; ++sidx) {
+            const uint32_t cc = D.stencil[(size_t)c * kStencil + sidx];
+            if (cc == kNone) break;
+            for (uint32_t j = D.cell_start[cc]; j < D.cell_start[cc + 1]; ++j) {
+                if (j == (uint32_t)i) continue;
+                float4 pj = pos[j];
+                float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+                float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+                float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+                float d2 = dist2_rn(dx, dy, dz);
+                if (d2 < P.rc2 && d2 > 0.0f) {
+                    float r = sqrtf(d2);
+                    float w = fmaxf(1.0f - r * P.inv_rc, 0.0f);
+                    float a = ONE_SPECIES ? P.a[0] : P.a[ti * P.n_species + __float_as_int(pj.w)];
+                    vir += 0.5 * (double)(a * w * r);
+                }
             }
         }
         if (P.has_bonds) {
@@ -485,6 +516,8 @@ int grid_for(int n)
     return g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g);
 }
 
+constexpr int kMaxDynSmem = 160 * 1024;  // largest staging buffer the brick builder accepts
+
 template <bool ONE, int MODE, bool LH>
 cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream_t s)
 {
@@ -511,6 +544,12 @@ cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, 
 }
 
 }  // namespace
+
+cudaError_t init_build_attributes(int max_dyn_smem);
+
+int max_brick_cap() { return kMaxDynSmem / (2 * (int)sizeof(float4)); }
+
+cudaError_t init_kernel_attributes() { return init_build_attributes(kMaxDynSmem); }
 
 int observe_blocks_for(int n) { return (n + kThreads - 1) / kThreads; }
 

@@ -22,6 +22,7 @@
 //              warp votes because each thread owns its particle's row)
 #include "dpd_internal.cuh"
 #include "dpd_math.cuh"
+#include "brick.cuh"
 
 namespace dpd {
 
@@ -270,134 +271,150 @@ __global__ void k_nbuild(SimParams P, Ptrs D)
     if ((threadIdx.x & 31) == 0) atomicMax(&D.ctl->max_nnb, local_max);
 }
 
-// Neighbour build staged through shared memory, one CTA per aligned brick of
-// kBrick^3 cells.  The CTA copies the positions of the brick's cells and of
-// the one-cell halo around it ((kBrick+2)^3 cells, each a contiguous range of
-// the cell-ordered arrays) into shared memory; then each thread takes one
-// particle of the brick and tests the particles of its 27 surrounding cells
-// from shared memory with the FP32 predicate, writing hits into its row in
-// the fixed stencil order (dz, dy, dx = -1..1): a deterministic row, built
-// without global gathers.  A brick whose halo holds more particles than the
-// shared buffer reads the overflow from global memory instead.
-constexpr int kBrick = 4;
-constexpr int kHalo = kBrick + 2;
-constexpr int kHaloCells = kHalo * kHalo * kHalo;  // 216
-constexpr int kBrickThreads = 256;
-constexpr int kBrickCap = 2816;                     // staged particles (44 KB)
+// Neighbour build, one CTA per brick (see brick.cuh).  The CTA stages the
+// positions of the brick's halo in shared memory with bulk (TMA) copies; each
+// thread owns one particle of the brick and tests the particles of its 27
+// surrounding cells, read from shared memory, with the FP32 predicate,
+// appending hits to its own row in the fixed stencil order (dz, dy, dx =
+// -1..1, each cell in index order): deterministic rows with no votes or
+// atomics.  Stencil cells whose nearest point lies beyond r_list are skipped.
+// A brick whose halo exceeds the staging buffer reads positions from global
+// memory.
+constexpr int kBuildThreads = 256;
 
-__global__ void __launch_bounds__(kBrickThreads) k_nbuild_brick(SimParams P, Ptrs D, int nbx, int nby)
+template <bool WRAP>
+__device__ __forceinline__ bool within_list(const SimParams &P, float4 pj, float4 pi)
+{
+    float dx, dy, dz;
+    if (WRAP) {
+        dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+        dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+        dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+    } else {
+        dx = __fsub_rn(pj.x, pi.x);
+        dy = __fsub_rn(pj.y, pi.y);
+        dz = __fsub_rn(pj.z, pi.z);
+    }
+    return dist2_rn(dx, dy, dz) < P.rlist2;
+}
+
+// Squared distance from a particle at fractional position f (in units of the
+// cell side, per axis) in its cell to the neighbour cell at offset o, along
+// the axis: 0 for the same slab, f for the slab below, 1 - f for the slab
+// above; times the squared side.  A cell whose nearest point is farther than
+// r_list (with a margin far above FP32 rounding of positions and cell
+// indices) holds no particle the predicate can admit and is skipped.
+__device__ __forceinline__ float slab_gap(float f, int o, float side)
+{
+    const float g = o < 0 ? f : (o > 0 ? 1.0f - f : 0.0f);
+    const float d = fmaxf(g * side - 1e-4f, 0.0f);
+    return d * d;
+}
+
+// Row of one particle: the particles of its 27 surrounding cells (stencil
+// order dz, dy, dx = -1..1, each cell in index order) that pass the FP32
+// predicate, as 32-bit global indices in the particle's row of its 32-wide
+// tile (entry k at k * 32).  Candidate positions come from the staged halo
+// (STAGED) or from global memory.
+template <bool WRAP, bool STAGED>
+__device__ __forceinline__ uint32_t build_row(const SimParams &P, const float4 *pos, const float4 *s_pos,
+                                              const uint32_t *s_off, const uint32_t *s_gstart,
+                                              const uint32_t *s_cnt, int hx, int hy, int hz, const float *frac,
+                                              uint32_t i, float4 pi, uint32_t *row, uint32_t cap)
+{
+    const float side[3] = {P.L[0] / (float)P.nc[0], P.L[1] / (float)P.nc[1], P.L[2] / (float)P.nc[2]};
+    uint32_t cnt = 0;
+    for (int oz = -1; oz <= 1; ++oz) {
+        const float gz = slab_gap(frac[2], oz, side[2]);
+        for (int oy = -1; oy <= 1; ++oy) {
+            const float gyz = gz + slab_gap(frac[1], oy, side[1]);
+            for (int ox = -1; ox <= 1; ++ox) {
+                if (gyz + slab_gap(frac[0], ox, side[0]) >= P.rlist2) continue;
+                const int t = brick_halo_slot(hx + ox, hy + oy, hz + oz);
+                const uint32_t o = s_off[t], g = s_gstart[t], n = s_cnt[t];
+                for (uint32_t e = 0; e < n; ++e) {
+                    const uint32_t j = g + e;
+                    const float4 pj = STAGED ? s_pos[o + e] : pos[j];
+                    const bool hit = within_list<WRAP>(P, pj, pi) & (j != i);
+                    if (hit & (cnt < cap)) row[(size_t)cnt * 32] = j;
+                    cnt += hit ? 1u : 0u;
+                }
+            }
+        }
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) k_nbuild_brick(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
-    __shared__ float4 s_pos[kBrickCap];
-    __shared__ uint32_t s_off[kHaloCells + 1];   // staged offset of each halo cell
-    __shared__ uint32_t s_gstart[kHaloCells];    // global start of each halo cell
+    extern __shared__ float4 s_pos[];  // [P.brick_cap] staged halo positions
+    __shared__ uint32_t s_off[kHaloCells + 1];
+    __shared__ uint32_t s_gstart[kHaloCells];
     __shared__ uint32_t s_cnt[kHaloCells];
-    __shared__ uint32_t s_wsum[kBrickThreads / 32];
-    __shared__ uint32_t s_lo, s_hi;
+    __shared__ uint32_t s_wsum[kBuildThreads / 32];
+    __shared__ __align__(8) uint64_t s_bar;
     const uint32_t par = D.ctl->parity;
     const float4 *pos = D.pos[par];
     const int b = blockIdx.x;
-    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-    const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
-    if (threadIdx.x == 0) {
-        s_lo = 0xFFFFFFFFu;
-        s_hi = 0u;
+    const BrickRange br = brick_halo(P, D, b, s_off, s_gstart, s_cnt, s_wsum);
+    const bool local = s_off[kHaloCells] <= (uint32_t)P.brick_cap;  // halo fits the staging buffer
+    bool staged = true;
+    if (local) staged = brick_stage_bulk(D, &s_bar, s_pos, pos, nullptr, nullptr, s_off, s_gstart, s_cnt);
+    if (!staged) {  // the error word is set; leave no rows behind for the force kernel
+        for (uint32_t i = br.lo + threadIdx.x; i < br.hi; i += blockDim.x) D.nnb[i] = 0u;
+        return;
     }
-    __syncthreads();
-    // 1. halo cell ranges
-    uint32_t cnt = 0;
-    if (threadIdx.x < kHaloCells) {
-        const int t = threadIdx.x;
-        const int hx = t % kHalo, hy = (t / kHalo) % kHalo, hz = t / (kHalo * kHalo);
-        const int cx = (x0 + hx - 1 + P.nc[0]) % P.nc[0];
-        const int cy = (y0 + hy - 1 + P.nc[1]) % P.nc[1];
-        const int cz = (z0 + hz - 1 + P.nc[2]) % P.nc[2];
-        const uint32_t r = D.rank_of_cell[(cz * P.nc[1] + cy) * P.nc[0] + cx];
-        const uint32_t st = D.cell_start[r];
-        cnt = D.cell_start[r + 1] - st;
-        s_gstart[t] = st;
-        s_cnt[t] = cnt;
-        const bool inner = hx >= 1 && hx <= kBrick && hy >= 1 && hy <= kBrick && hz >= 1 && hz <= kBrick &&
-                           x0 + hx - 1 < P.nc[0] && y0 + hy - 1 < P.nc[1] && z0 + hz - 1 < P.nc[2];
-        if (inner) {
-            atomicMin(&s_lo, st);
-            atomicMax(&s_hi, st + cnt);
-        }
-    }
-    // block exclusive scan of the counts -> staged offsets
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        uint32_t incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_wsum[warp] = incl;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += s_wsum[w];
-        if (threadIdx.x < kHaloCells) s_off[threadIdx.x] = before + incl - cnt;
-        if (threadIdx.x == kHaloCells - 1) s_off[kHaloCells] = before + incl;
-    }
-    __syncthreads();
-    // 2. stage positions: every thread copies elements e, e + blockDim, ... of
-    //    the concatenated halo ranges (its cell found by binary search over the
-    //    staged offsets), so all loads of a thread are independent
-    {
-        const uint32_t total = min(s_off[kHaloCells], (uint32_t)kBrickCap);
-        for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-            int a = 0, bnd = kHaloCells;  // find c with s_off[c] <= e < s_off[c + 1]
-            while (bnd - a > 1) {
-                const int mid = (a + bnd) >> 1;
-                if (s_off[mid] <= e) a = mid; else bnd = mid;
-            }
-            s_pos[e] = pos[s_gstart[a] + (e - s_off[a])];
-        }
-    }
-    __syncthreads();
-    // 3. one thread per particle of the brick
-    const uint32_t lo = s_lo, hi = s_hi;
+    const int bx = b % P.nb[0], by = (b / P.nb[0]) % P.nb[1], bz = b / (P.nb[0] * P.nb[1]);
+    const uint32_t cap = (uint32_t)P.cap;
+    const bool grid5 = P.nc[0] >= 5 && P.nc[1] >= 5 && P.nc[2] >= 5;
     uint32_t local_max = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const float4 pi = pos[i];
-        float fx, fy, fz;
-        const int cx = cell_axis(pi.x, P.cells_per_len[0], P.nc[0], &fx);
-        const int cy = cell_axis(pi.y, P.cells_per_len[1], P.nc[1], &fy);
-        const int cz = cell_axis(pi.z, P.cells_per_len[2], P.nc[2], &fz);
-        const int hx = cx - x0 + 1, hy = cy - y0 + 1, hz = cz - z0 + 1;  // 1..kBrick
-        uint32_t *row = D.nbr + (size_t)(i >> 5) * P.cap * 32 + (i & 31);
-        uint32_t n_hit = 0;
-        for (int oz = -1; oz <= 1; ++oz)
-            for (int oy = -1; oy <= 1; ++oy)
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int t = ((hz + oz) * kHalo + (hy + oy)) * kHalo + (hx + ox);
-                    const uint32_t o = s_off[t], n = s_cnt[t], st = s_gstart[t];
-                    for (uint32_t e = 0; e < n; ++e) {
-                        const uint32_t j = st + e;
-                        const float4 pj = (o + e < (uint32_t)kBrickCap) ? s_pos[o + e] : pos[j];
-                        const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-                        const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-                        const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-                        if (dist2_rn(dx, dy, dz) < P.rlist2 && j != i) {
-                            if (n_hit < (uint32_t)P.cap) row[(size_t)n_hit * 32] = j;
-                            ++n_hit;
-                        }
-                    }
-                }
-        if (n_hit > (uint32_t)P.cap) atomicOr(&D.ctl->err, kErrNbrOverflow);
-        D.nnb[i] = n_hit < (uint32_t)P.cap ? n_hit : (uint32_t)P.cap;
-        local_max = n_hit > local_max ? n_hit : local_max;
+    const uint32_t nloc = br.hi - br.lo;
+    for (uint32_t p0 = 0; p0 < nloc; p0 += blockDim.x) {
+        const uint32_t p = p0 + threadIdx.x;
+        const bool valid = p < nloc;
+        const uint32_t i = br.lo + p;
+        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cx = 1, cy = 1, cz = 1;
+        float fx_ = 0.f, fy_ = 0.f, fz_ = 0.f;
+        if (valid) {
+            pi = pos[i];
+            cx = cell_axis(pi.x, P.cells_per_len[0], P.nc[0], &fx_);
+            cy = cell_axis(pi.y, P.cells_per_len[1], P.nc[1], &fy_);
+            cz = cell_axis(pi.z, P.cells_per_len[2], P.nc[2], &fz_);
+        }
+        const int hx = cx - bx * kBrick + 1, hy = cy - by * kBrick + 1, hz = cz - bz * kBrick + 1;  // 1..kBrick
+        // a cell one layer or more inside a grid of >= 5 cells per axis never
+        // sees a periodic image in its stencil: the whole warp can skip the
+        // minimum image when all its particles sit in such cells
+        const bool inner = grid5 && cx >= 1 && cx <= P.nc[0] - 2 && cy >= 1 && cy <= P.nc[1] - 2 && cz >= 1 &&
+                           cz <= P.nc[2] - 2;
+        const bool warp_inner = __all_sync(0xFFFFFFFFu, inner || !valid);
+        if (!valid) continue;
+        uint32_t *row = D.nbr + (size_t)(i >> 5) * cap * 32 + (i & 31u);
+        const float frac[3] = {fx_, fy_, fz_};
+        uint32_t cnt;
+        if (local)
+            cnt = warp_inner ? build_row<false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap)
+                             : build_row<true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+        else
+            cnt = build_row<true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+        if (cnt > cap) atomicOr(&D.ctl->err, kErrNbrOverflow);
+        D.nnb[i] = min(cnt, cap);
+        local_max = max(local_max, cnt);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, local_max, o);
-        local_max = y > local_max ? y : local_max;
-    }
+    for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xFFFFFFFFu, local_max, o));
     if ((threadIdx.x & 31) == 0 && local_max) atomicMax(&D.ctl->max_nnb, local_max);
 }
 
 }  // namespace
 
 int scan_blocks_for(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
+
+cudaError_t init_build_attributes(int max_dyn_smem)
+{
+    return cudaFuncSetAttribute(k_nbuild_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+}
 
 cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, int n_scan_blocks)
 {
@@ -414,10 +431,8 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
     else
         k_gather<false><<<gg, kThreads, 0, s>>>(P, D);
     k_commit<<<1, 1, 0, s>>>(D);
-    if (P.nc[0] >= 3 && P.nc[1] >= 3 && P.nc[2] >= 3) {
-        const int nbx = (P.nc[0] + kBrick - 1) / kBrick, nby = (P.nc[1] + kBrick - 1) / kBrick;
-        const int nbz = (P.nc[2] + kBrick - 1) / kBrick;
-        k_nbuild_brick<<<nbx * nby * nbz, kBrickThreads, 0, s>>>(P, D, nbx, nby);
+    if (P.use_bricks) {
+        k_nbuild_brick<<<P.nbricks, kBuildThreads, sizeof(float4) * (size_t)P.brick_cap, s>>>(P, D);
     } else {
         k_nbuild<<<g, kThreads, 0, s>>>(P, D);
     }

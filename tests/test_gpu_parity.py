@@ -47,7 +47,10 @@ def test_pair_rng_extreme_words():
     assert np.abs(xi - xr).max() < 2e-5 * max(1.0, np.abs(xr).max())
 
 
-@pytest.mark.parametrize("name", ["fluid_small", "poiseuille_small", "amphiphile_small"])
+ALL = ["fluid_small", "poiseuille_small", "amphiphile_small", "dense_small", "tiny_box"]
+
+
+@pytest.mark.parametrize("name", ALL)
 def test_neighbors_bit_exact(name):
     st, cfg, box, bonds = _workload(name)
     g, o = make_pair(cfg, box=box)
@@ -61,6 +64,18 @@ def test_neighbors_bit_exact(name):
 
 
 def _workload(name):
+    if name == "dense_small":
+        # rho = 8: brick halos overflow the staging buffer (global-index rows)
+        box = (8.0, 8.0, 8.0)
+        x, v = workloads.uniform_fluid(box, 4096, 1.0, 77)
+        cfg = dict(workloads.CONFIGS["fluid_small"], box=box)
+        return dict(x=x, v=v, species=None, n=4096), cfg, box, None
+    if name == "tiny_box":
+        # 2 cells per axis: no bricks, the per-particle builder and force path
+        box = (3.2, 3.5, 2.9)
+        x, v = workloads.uniform_fluid(box, 98, 1.0, 78)
+        cfg = dict(workloads.CONFIGS["fluid_small"], box=box)
+        return dict(x=x, v=v, species=None, n=98), cfg, box, None
     if name == "fluid_small":
         st = workloads.make("fluid_small")
         return st, st["cfg"], st["cfg"]["box"], None
@@ -73,7 +88,7 @@ def _workload(name):
     raise KeyError(name)
 
 
-@pytest.mark.parametrize("name", ["fluid_small", "poiseuille_small", "amphiphile_small"])
+@pytest.mark.parametrize("name", ALL)
 def test_forces_match_oracle(name):
     st, cfg, box, bonds = _workload(name)
     g, o = make_pair(cfg, box=box, bonds=bonds)
