@@ -160,9 +160,19 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = workloads.CONFIGS[args.workload]
-    sub = (30.0, 30.0, 30.0)
-    st = workloads.make(args.workload, box=sub)
     import oracle
+    # size the sub-box so that warm-up + timed steps take about a minute:
+    # time a short probe run, then scale the particle count
+    probe = workloads.make(args.workload, box=(8.0, 8.0, 8.0))
+    psys = oracle.System((8.0, 8.0, 8.0), cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"],
+                         lam=cfg["lam"])
+    t0 = time.perf_counter()
+    psys.run(probe["x"], probe["v"], 10)
+    rate = probe["n"] * 10 / max(time.perf_counter() - t0, 1e-6)
+    n_target = rate * 60.0 / max(args.steps + args.warmup, 1)
+    Ls = float(min(30.0, max(6.0, round((n_target / cfg["rho"]) ** (1.0 / 3.0)))))
+    sub = (Ls, Ls, Ls)
+    st = workloads.make(args.workload, box=sub)
     sysm = oracle.System(sub, cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"], lam=cfg["lam"])
     f, _ = sysm.forces(st["x"], st["v"], step=0)
     res = sysm.run(st["x"], st["v"], args.warmup, f=f)
@@ -177,8 +187,8 @@ def run_reference(args):
         "config": {"workload": "%s: periodic L=100 rho=3 DPD fluid (3,000,000 particles), a=25 gamma=4.5 kT=1 "
                                "s=1 dt=0.01" % args.workload, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "FP64 oracle (single-threaded C), each step on a 30^3 sub-box of the same "
-                                   "fluid (%d particles, rho=3)" % st["n"]},
+                         "sample": "FP64 oracle (single-threaded C), each step on a %g^3 sub-box of the same "
+                                   "fluid (%d particles, rho=3), sized for about a minute of work" % (Ls, st["n"])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -305,7 +315,7 @@ def main():
         "gpu_launches": launches,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        sample_steps = 2
+        sample_steps = 1
         rate, secs = oracle_rate(xo, vo, cfg, sample_steps, cfg["box"])
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "FP64 oracle (single-threaded C), %d steps of the full %d-particle box "

@@ -311,17 +311,22 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             head += 32u;
         }
     };
-    // 32-bit rows, entry k at k * 32: the row entry and position of
-    // candidate k+1 are loaded while candidate k is tested
-    uint32_t jc = self;
-    if (cnt > 0) jc = __ldg(row + lane);
-    float4 pc = __ldg(pos + jc);
+    // 32-bit rows, entry k at k * 32.  Row entries are loaded four candidates
+    // ahead through a register rotation (the loop stays rolled: the batch
+    // evaluation inside it is large), and each candidate's position one ahead.
+    uint32_t q0 = cnt > 0 ? __ldg(row + lane) : self;
+    uint32_t q1 = cnt > 1 ? __ldg(row + 32 + lane) : self;
+    uint32_t q2 = cnt > 2 ? __ldg(row + 64 + lane) : self;
+    uint32_t q3 = cnt > 3 ? __ldg(row + 96 + lane) : self;
+    float4 pc = __ldg(pos + q0);
     for (int k = 0; k < maxcnt; ++k) {
-        uint32_t jn = self;
-        if (k + 1 < cnt) jn = __ldg(row + (size_t)(k + 1) * 32 + lane);
-        const float4 pn = __ldg(pos + jn);
-        candidate(k, jc, pc);
-        jc = jn;
+        const uint32_t q4 = k + 4 < cnt ? __ldg(row + (size_t)(k + 4) * 32 + lane) : self;
+        const float4 pn = __ldg(pos + q1);
+        candidate(k, q0, pc);
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        q3 = q4;
         pc = pn;
     }
     while (tail != head) {
