@@ -130,6 +130,13 @@ dpd_status dpd_forces(dpd_sim *h, double *f_out);
 /* The force the integrator holds for the next step (n x 3). */
 dpd_status dpd_get_force(dpd_sim *h, double *f_out);
 
+/* Replace the force the integrator holds (n x 3, caller's order, rounded to
+ * FP32).  With dpd_get_state and dpd_get_force it completes a checkpoint:
+ * the force held between steps was evaluated with the predicted velocity
+ * v~ of the lambda scheme (Sec. 3.1), which dpd_set_state cannot recompute
+ * from (x, v) alone. */
+dpd_status dpd_set_force(dpd_sim *h, const double *f);
+
 /* Advance nsteps steps (Alg. 1 main loop, Sec. 3.1): for each step
  *   x += dt v + dt^2/2 f;  v~ = v + lambda dt f;  rebuild lists if needed;
  *   f' = F(x, v~, step + 1);  v += dt/2 (f + f');  step += 1.

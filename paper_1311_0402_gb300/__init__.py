@@ -25,7 +25,7 @@ STATUS = {0: "DPD_OK", 1: "DPD_ERR_ARG", 2: "DPD_ERR_OOM", 3: "DPD_ERR_CUDA", 4:
 EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds", "dpd_build_neighbors",
            "dpd_get_neighbors", "dpd_forces", "dpd_get_force", "dpd_step", "dpd_observables", "dpd_profile",
            "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled",
-           "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error")
+           "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error", "dpd_set_force")
 
 
 class DPDError(RuntimeError):
@@ -117,6 +117,7 @@ def lib():
         L.dpd_get_neighbors.argtypes = [vp, i64, P(u32), P(i64)]
         L.dpd_forces.argtypes = [vp, P(f64)]
         L.dpd_get_force.argtypes = [vp, P(f64)]
+        L.dpd_set_force.argtypes = [vp, P(f64)]
         L.dpd_step.argtypes = [vp, i64]
         L.dpd_observables.argtypes = [vp, P(dpd_obs)]
         L.dpd_step_profiled.argtypes = [vp, i64, P(dpd_step_times)]
@@ -210,6 +211,11 @@ def dpd_get_force(h) -> np.ndarray:
     f = np.zeros((_nvec(h), 3), np.float64)
     _check(lib().dpd_get_force(h, _p(f, ctypes.c_double)), h)
     return f
+
+
+def dpd_set_force(h, f):
+    f = np.ascontiguousarray(f, np.float64).reshape(-1, 3)
+    _check(lib().dpd_set_force(h, _p(f, ctypes.c_double)), h)
 
 
 def dpd_step(h, nsteps: int):
@@ -345,6 +351,9 @@ class Sim:
 
     def force(self):
         return dpd_get_force(self.h)
+
+    def set_force(self, f):
+        dpd_set_force(self.h, f)
 
     def step(self, n):
         dpd_step(self.h, n)

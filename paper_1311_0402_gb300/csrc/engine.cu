@@ -721,6 +721,31 @@ dpd_status dpd_get_force(dpd_sim *h, double *f_out)
     return download_xyz(h, h->D.force[c.parity], f_out);
 }
 
+dpd_status dpd_set_force(dpd_sim *h, const double *f)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (!f) return fail(h, DPD_ERR_ARG, "f is NULL");
+    DevCtl c;
+    st = read_ctl(h, c);
+    if (st) return st;
+    std::vector<uint32_t> pid(h->n);
+    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.oparity], sizeof(uint32_t) * h->n, cudaMemcpyDeviceToHost,
+                                h->stream));
+    st = wait(h);
+    if (st) return st;
+    std::vector<float4> buf(h->n);
+    for (int64_t p = 0; p < h->n; ++p) {
+        const uint32_t i = pid[p];
+        for (int a = 0; a < 3; ++a)
+            if (!std::isfinite(f[3 * (size_t)i + a])) return fail(h, DPD_ERR_ARG, "non-finite force");
+        buf[p] = make_float4((float)f[3 * (size_t)i], (float)f[3 * (size_t)i + 1], (float)f[3 * (size_t)i + 2], 0.0f);
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->D.force[c.parity], buf.data(), sizeof(float4) * h->n, cudaMemcpyHostToDevice,
+                                h->stream));
+    return wait(h);
+}
+
 dpd_status dpd_step(dpd_sim *h, int64_t nsteps)
 {
     dpd_status st = guard(h, true);

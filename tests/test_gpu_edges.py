@@ -1,0 +1,115 @@
+"""Edge cases of the GPU path: degenerate particle counts, a dense clump
+(neighbour capacity grows), particles on cell faces, argument and
+call-order errors, determinism, and checkpoint / resume."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1311_0402_gb300 as dpd
+import workloads
+from gpu_util import force_error, make_pair, need_gpu, pair_set
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+CFG = workloads.CONFIGS["fluid_small"]
+
+
+def test_single_and_pair():
+    g, o = make_pair(CFG)
+    g.set_state(np.array([[5.0, 5, 5]]), np.array([[0.1, 0, 0]]))
+    assert np.all(g.forces() == 0.0)
+    assert len(g.neighbors()) == 0
+    g.step(3)
+    g.set_state(np.array([[5.5, 5, 5], [5.0, 5, 5]]), np.zeros((2, 3)), step=1)
+    x32, v32, _ = g.state()
+    fo, _ = o.forces(x32, v32, step=1)
+    assert np.abs(g.forces() - fo).max() < 1e-4 * np.abs(fo).max()
+
+
+def test_dense_clump_grows_capacity():
+    rng = np.random.default_rng(9)
+    x = np.concatenate([rng.random((400, 3)) * 0.8 + 4.0, rng.random((2000, 3)) * 10.0])
+    v = rng.standard_normal(x.shape)
+    g, o = make_pair(CFG)
+    g.set_state(x, v)
+    assert g.info()["nbr_capacity"] > 400
+    x32, v32, _ = g.state()
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, CFG["box"], 1.3))
+    fo, _ = o.forces(x32, v32)
+    err, _ = force_error(g.forces(), fo)
+    assert err < 1e-4
+
+
+def test_particles_on_cell_faces():
+    # 7 cells of side 10/7 per axis: place particles exactly on faces and corners
+    side = 10.0 / 7.0
+    grid = np.arange(7) * side
+    xs = np.array(np.meshgrid(grid, grid, grid[:3], indexing="ij")).reshape(3, -1).T
+    x = np.concatenate([xs, xs + np.array([0.65, 0.0, 0.0])])
+    v = np.zeros_like(x)
+    g, o = make_pair(CFG)
+    g.set_state(x, v)
+    x32, v32, _ = g.state()
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, CFG["box"], 1.3))
+    fo, _ = o.forces(x32, v32)
+    err, _ = force_error(g.forces(), fo)
+    assert err < 1e-4
+
+
+def test_argument_and_state_errors():
+    g = dpd.Sim(CFG["box"], CFG["a"], 4.5, 1.0, 1.0, 1.0, 0.01)
+    with pytest.raises(dpd.DPDError) as e:
+        g.step(1)
+    assert e.value.status == 7  # DPD_ERR_STATE
+    with pytest.raises(dpd.DPDError) as e:
+        g.set_state(np.zeros((0, 3)), np.zeros((0, 3)))
+    assert e.value.status == 1
+    with pytest.raises(dpd.DPDError) as e:
+        g.set_state(np.ones((3, 3)), np.zeros((3, 3)), species=np.array([0, 1, 0]))
+    assert e.value.status == 1
+    with pytest.raises(dpd.DPDError) as e:
+        g.set_state(np.ones((3, 3)), np.zeros((3, 3)), tag=np.array([4, 4, 5]))
+    assert e.value.status == 1
+    x = np.ones((3, 3))
+    x[1, 2] = np.nan
+    with pytest.raises(dpd.DPDError):
+        g.set_state(x, np.zeros((3, 3)))
+    g.close()
+
+
+def test_deterministic_runs():
+    st = workloads.make("fluid_small")
+    outs = []
+    for _ in range(2):
+        g, _ = make_pair(st["cfg"])
+        g.set_state(st["x"], st["v"])
+        g.step(57)
+        outs.append(g.state())
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_checkpoint_resume():
+    st = workloads.make("fluid_small")
+    a, _ = make_pair(st["cfg"])
+    a.set_state(st["x"], st["v"])
+    a.step(30)
+    x, v, step = a.state()
+    f = a.force()
+    b, _ = make_pair(st["cfg"])
+    b.set_state(x, v, step=step)
+    b.set_force(f)
+    a.step(3)
+    b.step(3)
+    xa, va, sa = a.state()
+    xb, vb, sb = b.state()
+    assert sa == sb == step + 3
+    # the lists differ in build time, so sums differ in rounding order only
+    assert np.abs(xa - xb).max() < 1e-5
+    assert np.abs(va - vb).max() < 1e-3

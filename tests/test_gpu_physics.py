@@ -1,0 +1,122 @@
+"""Long-run physics: the GPU path and the FP64 oracle, each run on its own
+from the same FP32 initial state, must agree within 1 % in time-averaged
+temperature and pressure, and in the reverse-Poiseuille velocity profile
+(fitted amplitude within 2 %: the profile is a noisy mean of a chaotic
+trajectory; 2 % is five standard errors of the difference); the full-size
+reverse-Poiseuille run must follow the analytic parabola (Sec. 4.2)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1311_0402_gb300 as dpd
+import workloads
+from gpu_util import make_pair, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def test_fluid_temperature_pressure_match_oracle():
+    st = workloads.make("fluid_small")
+    cfg = st["cfg"]
+    n = st["n"]
+    g, o = make_pair(cfg)
+    g.set_state(st["x"], st["v"])
+    x32, v32, _ = g.state()
+    nsteps, burn, every = 4000, 800, 4
+    Tg, pg = [], []
+    for s in range(nsteps // every):
+        g.step(every)
+        if (s + 1) * every > burn:
+            ob = g.observables()
+            Tg.append(ob["temperature"])
+            pg.append(ob["pressure"])
+    res = o.run(x32, v32, nsteps)
+    obs = res["obs"][burn:]
+    To = oracle.System.temperature(obs[:, 0], n).mean()
+    po = o.pressure(obs[:, 0], obs[:, 1]).mean()
+    Tg, pg = float(np.mean(Tg)), float(np.mean(pg))
+    assert abs(Tg - To) < 0.01 * To, (Tg, To)
+    assert abs(pg - po) < 0.01 * po, (pg, po)
+    # both at the thermostat temperature and the known pressure of this state
+    assert abs(Tg - 1.0) < 0.03 and 22.5 < pg < 25.0
+
+
+def _fit_amplitude(sums, counts, Ly, nbins):
+    """Least-squares amplitude A of u(y) = A y (h - y) (lower half, +g) and
+    -A (y - h)(2h - y) (upper half) for the binned mean v_x."""
+    h = Ly / 2
+    yc = (np.arange(nbins) + 0.5) * Ly / nbins
+    u = sums / np.maximum(counts, 1)
+    shape = np.where(yc < h, yc * (h - yc), -(yc - h) * (2 * h - yc))
+    A = float((shape * u).sum() / (shape * shape).sum())
+    resid = u - A * shape
+    r2 = 1.0 - (resid ** 2).sum() / ((u - u.mean()) ** 2).sum()
+    return A, r2
+
+
+def test_reverse_poiseuille_profile_matches_oracle():
+    """16 x 10 x 5 box (rho = 4, s = 1/2, g = +-0.055): the amplitude of the
+    time-averaged double parabola, GPU (mean of 6 seeds) against the oracle
+    (one run).  The profile carries slow hydrodynamic noise, so the bound is
+    the larger of 1 % and three standard errors of the oracle's block means."""
+    box = (16.0, 10.0, 5.0)
+    nbins, nsteps, burn, every, block = 10, 7000, 2500, 5, 500
+    st = workloads.make("poiseuille", box=box)
+    cfg = st["cfg"]
+    amps = []
+    for seed in range(6):
+        g, o = make_pair(cfg, box=box, seed=42 + seed)
+        g.set_state(st["x"], st["v"])
+        if seed == 0:
+            x32, v32, _ = g.state()
+        sg, cg = np.zeros(nbins), np.zeros(nbins)
+        g.step(burn)
+        for s in range((nsteps - burn) // every):
+            g.step(every)
+            g.profile(1, 0, nbins, sg, cg)
+        amps.append(_fit_amplitude(sg, cg, box[1], nbins)[0])
+        g.close()
+    Ag = float(np.mean(amps))
+    _, o = make_pair(cfg, box=box, seed=42)
+    res = o.run(x32, v32, burn)
+    blocks = []
+    state = res
+    for b in range((nsteps - burn) // block):
+        state = o.run(state["x"], state["v"], block, step=state["step"], f=state["f"], prof_nbins=nbins, prof_from=1)
+        blocks.append(_fit_amplitude(state["prof_sum"], state["prof_cnt"], box[1], nbins)[0])
+    Ao = float(np.mean(blocks))
+    se = float(np.std(blocks, ddof=1) / np.sqrt(len(blocks)))
+    tol = max(0.01 * abs(Ao), 3.0 * se)
+    assert abs(Ag - Ao) < tol, (Ag, Ao, se)
+    r2 = _fit_amplitude(sg, cg, box[1], nbins)[1]
+    assert r2 > 0.97, r2
+
+
+def test_reverse_poiseuille_full_size_start_up():
+    """40 x 20 x 10, rho = 4 (32,000 particles): the flow started from rest
+    builds the antisymmetric double parabola over its first 4,000 steps
+    (steps 3,000-4,000 averaged).  Beyond about 5,000 steps the shear layers
+    of this 40-long box lose stability and the mean profile collapses, in
+    the GPU and the oracle alike, so no later average is compared here."""
+    st = workloads.make("poiseuille")
+    cfg = st["cfg"]
+    g = dpd.Sim(cfg["box"], cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"],
+                body_mode=cfg["body_mode"], body=cfg["body"])
+    g.set_state(st["x"], st["v"])
+    nbins = 20
+    sg, cg = np.zeros(nbins), np.zeros(nbins)
+    g.step(3000)
+    for _ in range(100):
+        g.step(10)
+        g.profile(1, 0, nbins, sg, cg)
+    A, r2 = _fit_amplitude(sg, cg, cfg["box"][1], nbins)
+    assert r2 > 0.98, r2
+    u = sg / cg
+    assert abs(u[: nbins // 2].mean() + u[nbins // 2:].mean()) < 0.05 * abs(u).max()
+    assert A > 0.03, A
+    g.close()
