@@ -61,6 +61,14 @@ typedef struct {
     double body_force[3];     /* g (force per particle, unit mass) */
     int32_t nbr_capacity;     /* neighbours per particle; 0 = from density */
     int32_t graph_steps;      /* steps per captured CUDA graph (default 8; 0 = no graphs) */
+    int32_t deterministic;    /* 0 (default): each pair is evaluated once and its force is
+                                 added to the second particle with float atomics, so force
+                                 sums are not bitwise reproducible run to run; 1: every
+                                 pair is evaluated by both particles and each force is
+                                 summed in a fixed order (bit-identical runs, about 1.5x
+                                 the pair work).  Random numbers and neighbour sets are
+                                 deterministic in both modes. */
+    int32_t reserved;         /* must be 0 */
     double wait_timeout_s;    /* host wait limit per call (default 600 s) */
     void *stream;             /* cudaStream_t to run on; NULL = a stream of the handle */
 } dpd_options;

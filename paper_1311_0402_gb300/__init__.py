@@ -44,6 +44,8 @@ class dpd_options(ctypes.Structure):
         ("body_force", ctypes.c_double * 3),
         ("nbr_capacity", ctypes.c_int32),
         ("graph_steps", ctypes.c_int32),
+        ("deterministic", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("wait_timeout_s", ctypes.c_double),
         ("stream", ctypes.c_void_p),
     ]
@@ -309,7 +311,8 @@ class Sim:
     """A DPD system on the GPU (one handle of libdpd.so)."""
 
     def __init__(self, box, a_ij, gamma, kT, rc, s, dt, lam=0.5, skin=0.3, seed=42, body_mode=0,
-                 body=(0.0, 0.0, 0.0), rebuild_every=0, nbr_capacity=0, graph_steps=8, stream=None):
+                 body=(0.0, 0.0, 0.0), rebuild_every=0, nbr_capacity=0, graph_steps=8, stream=None,
+                 deterministic=0):
         o = dpd_default_options()
         o.skin = skin
         o.lam = lam
@@ -319,6 +322,7 @@ class Sim:
         o.rebuild_every = rebuild_every
         o.nbr_capacity = nbr_capacity
         o.graph_steps = graph_steps
+        o.deterministic = 1 if deterministic else 0
         o.stream = stream
         self.box = np.asarray(box, np.float64)
         self.h = dpd_create(box, a_ij, gamma, kT, rc, s, dt, o)

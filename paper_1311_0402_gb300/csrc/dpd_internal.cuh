@@ -46,8 +46,8 @@ struct DevCtl {
     unsigned long long step; // step number of the live state
     unsigned long long nrebuild;
     uint32_t max_nnb;        // largest neighbour count of the last build
-    uint32_t rebuild_next;   // displacement flags raised by the kernel running now
-    uint32_t done;           // finished blocks of the kernel running now
+    uint32_t rebuild_next;   // displacement flag raised by the kernel running now
+    uint32_t pad0;
     uint32_t oparity;        // live set of the order arrays (tag, pid): flips only at a rebuild
 };
 
@@ -77,7 +77,8 @@ struct SimParams {
     float a[kMaxSpecies * kMaxSpecies];
     float k_bond, r0_bond;
     int has_bonds;
-    int use_bricks;           // every axis has >= 3 cells: brick kernels, brick-local rows
+    int newton3;              // half rows (j > i), each pair once, partner force by atomics
+    int use_bricks;           // every axis has >= 3 cells: the brick-staged builder
     int brick_cap;            // halo particles the brick builder stages in shared memory
     int nb[3];                // bricks per axis
     int nbricks;
@@ -87,6 +88,8 @@ struct Ptrs {
     float4 *pos[2], *vel[2], *vkick[2], *force[2];
     uint32_t *tag[2], *pid[2];
     float4 *xref;             // positions at the last rebuild
+    float4 *fown;             // Newton-3 mode: each particle's own-row force sum
+    float4 *facc;             // Newton-3 mode: forces added by other particles' rows (atomics)
     float4 *fout;             // output of a standalone force evaluation
     DevCtl *ctl;
     // cells
@@ -127,6 +130,8 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
 // buffer set (flips the live set, advances the step).  kForceFinish: force,
 // then phase 2 only (full-step velocity and force into the other set).
 enum ForceMode { kForceEval = 0, kForceStep = 1, kForceFinish = 2 };
+// In Newton-3 mode the pair kernel only accumulates (fown, facc) and a
+// settle kernel completes the same mode afterwards; launch_force runs both.
 cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s);
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s);
 cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int vel_axis, int nbins,

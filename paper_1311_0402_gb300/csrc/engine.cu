@@ -218,7 +218,7 @@ void drop_graphs(dpd_sim *h)
     h->timed_graphs.clear();
 }
 
-constexpr int kRebuildKernels = 9;  // bin, 3 scan, scatter, rank, gather, commit, nbuild (+ brick tiles)
+constexpr int kRebuildKernels = 9;  // bin, 3 scan, scatter, rank, gather, commit, nbuild
 
 // Timing event on the stream; inside a graph capture it becomes an event
 // record node whose timestamp stays readable after the graph runs.
@@ -316,6 +316,8 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     }
     A((void **)&D.xref, f4);
     A((void **)&D.fout, f4);
+    A((void **)&D.fown, f4);
+    A((void **)&D.facc, f4);
     A((void **)&D.key, u4);
     A((void **)&D.slot, u4);
     A((void **)&D.tmp_idx, u4);
@@ -330,6 +332,7 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     if (st) return st;
     CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(D.nnb, 0, u4, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(D.facc, 0, f4, h->stream));
     h->P.cap = cap;
     h->cap_alloc_n = n;
     return DPD_OK;
@@ -404,6 +407,8 @@ void dpd_default_options(dpd_options *o)
     o->lambda = 0.5;
     o->nbr_capacity = 0;
     o->graph_steps = 8;
+    o->deterministic = 0;
+    o->reserved = 0;
     o->wait_timeout_s = 600.0;
     o->stream = nullptr;
 }
@@ -482,6 +487,7 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     for (int k = 0; k < n_species * n_species; ++k) P.a[k] = (float)a_ij[k];
     P.body_mode = o.body_force_mode;
     P.rebuild_every = o.rebuild_every;
+    P.newton3 = o.deterministic ? 0 : 1;
     P.key[0] = (uint32_t)(o.seed & 0xFFFFFFFFull);
     P.key[1] = (uint32_t)(o.seed >> 32);
     P.key[2] = 0x243F6A88u;
@@ -615,6 +621,7 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
     CUDA_TRY(h, cudaMemcpyAsync(D.pid[0], pid.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
     if (!h->P.lambda_half) CUDA_TRY(h, cudaMemsetAsync(D.vkick[0], 0, sizeof(float4) * n, h->stream));
     CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(D.facc, 0, sizeof(float4) * n, h->stream));
     DevCtl c;
     std::memset(&c, 0, sizeof(c));
     c.step = step;
@@ -683,8 +690,8 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
         for (uint32_t k = 0; k < nnb[i]; ++k) {
             const uint32_t j = row[(size_t)k * 32];
             if (j >= (uint32_t)n) return fail(h, DPD_ERR_STATE, "neighbour index out of range");
-            const uint32_t a = pid[i], b2 = pid[j];
-            if (a < b2) pr.push_back(((uint64_t)a << 32) | b2);
+            const uint32_t a = std::min(pid[i], pid[j]), b2 = std::max(pid[i], pid[j]);
+            if (a != b2) pr.push_back(((uint64_t)a << 32) | b2);
         }
     }
     std::sort(pr.begin(), pr.end());
@@ -848,7 +855,8 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
         }
         out->steps = nsteps;
         out->force_launches = nsteps;
-        out->kernel_launches = nsteps * (1 + kRebuildKernels + (h->P.use_bricks ? 1 : 0)) + 1;
+        // per step: chain, force (+ settle), advance; plus the opening phase 1 + advance
+        out->kernel_launches = nsteps * (2 + kRebuildKernels + (h->P.newton3 ? 1 : 0)) + 2;
         out->rebuilds = (int64_t)(c.nrebuild - c0.nrebuild);
     }
     return DPD_OK;

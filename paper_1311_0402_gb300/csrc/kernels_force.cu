@@ -21,32 +21,31 @@ __device__ __forceinline__ float wrap_pos(float x, float L, float invL)
     return x;
 }
 
-// End-of-block bookkeeping of the kernels that move particles.  Every block
-// reports whether one of its particles crossed the displacement threshold;
-// the last block to finish (all others have completed their reads and
-// writes) publishes the rebuild flag for the chain that follows and, when
-// `advance` is set, makes the buffer set it wrote the live one and advances
-// the step counter.
-__device__ __forceinline__ void finish_block(const SimParams &P, DevCtl *ctl, bool moved, bool advance, bool check_every)
+// End of a kernel that moves particles: a block any of whose particles
+// crossed the displacement threshold raises rebuild_next (a plain store of
+// the same value from every such block).  k_advance, launched right after,
+// publishes it and flips the buffer set; no block counts the others.
+__device__ __forceinline__ void finish_block(DevCtl *ctl, bool moved)
 {
-    const bool any = __syncthreads_or(moved);
-    if (threadIdx.x == 0) {
-        if (any) atomicOr(&ctl->rebuild_next, 1u);
-        __threadfence();
-        const uint32_t prev = atomicAdd(&ctl->done, 1u);
-        if (prev == gridDim.x - 1) {
-            __threadfence();
-            uint32_t next = atomicExch(&ctl->rebuild_next, 0u);
-            if (check_every && P.rebuild_every > 0 && ctl->since_rebuild + 1u >= (uint32_t)P.rebuild_every) next = 1u;
-            ctl->rebuild = next;
-            ctl->done = 0u;
-            if (advance) {
-                ctl->parity ^= 1u;
-                ctl->step += 1ull;
-                ctl->since_rebuild += 1u;
-            }
-            __threadfence();
-        }
+    if (__syncthreads_or(moved) && threadIdx.x == 0) ctl->rebuild_next = 1u;
+}
+
+// One thread, after a moving kernel: the rebuild flag for the chain that
+// follows (also raised when rebuild_every steps have passed), and, when the
+// kernel integrated into the other buffer set, that set becomes the live one
+// and the step advances.
+template <bool ADVANCE, bool CHECK_EVERY>
+__global__ void k_advance(SimParams P, Ptrs D)
+{
+    DevCtl *c = D.ctl;
+    uint32_t next = c->rebuild_next;
+    if (CHECK_EVERY && P.rebuild_every > 0 && c->since_rebuild + 1u >= (uint32_t)P.rebuild_every) next = 1u;
+    c->rebuild = next;
+    c->rebuild_next = 0u;
+    if (ADVANCE) {
+        c->parity ^= 1u;
+        c->step += 1ull;
+        c->since_rebuild += 1u;
     }
 }
 
@@ -91,7 +90,7 @@ __global__ void k_phase1(SimParams P, Ptrs D)
         }
         moved |= moved_beyond(P, x, D.xref[i]);
     }
-    finish_block(P, ctl, moved, false, true);
+    finish_block(ctl, moved);
 }
 
 __global__ void k_signature(SimParams P, Ptrs D)
@@ -107,16 +106,11 @@ __global__ void k_signature(SimParams P, Ptrs D)
     }
 }
 
-// Epilogue of the force kernels for particle i: bonds, body force, then per
-// MODE the force is stored, or the step is integrated into the other buffer
-// set.  Returns whether the particle moved past the rebuild threshold.
-template <int MODE, bool LHALF>
-__device__ __forceinline__ bool force_epilogue(const SimParams &P, const Ptrs &D, DevCtl *ctl, int i, float4 pi,
-                                               float4 vi, float fx, float fy, float fz, uint32_t par, uint32_t opar,
-                                               unsigned long long step0, int out_fout)
+// Bonds (Sec. 4.5) and the body force (Sec. 4.2) on particle i, added to f.
+__device__ __forceinline__ void add_bonds_body(const SimParams &P, const Ptrs &D, int i, float4 pi,
+                                               const float4 *__restrict__ pos, uint32_t opar, float &fx,
+                                               float &fy, float &fz)
 {
-    bool moved = false;
-    const float4 *__restrict__ pos = D.pos[par];
     if (P.has_bonds) {
         const uint32_t id = D.pid[opar][i];
         const uint32_t *bp = D.bond_partner + (size_t)id * kMaxBonds;
@@ -145,6 +139,17 @@ __device__ __forceinline__ bool force_epilogue(const SimParams &P, const Ptrs &D
         const float sg = pi.y < P.halfL[1] ? 1.0f : -1.0f;
         fx = fmaf(sg, P.body[0], fx); fy = fmaf(sg, P.body[1], fy); fz = fmaf(sg, P.body[2], fz);
     }
+}
+
+// Final stage of a force evaluation for particle i with total force f: per
+// MODE the force is stored, or the step is integrated into the other buffer
+// set.  Returns whether the particle moved past the rebuild threshold.
+template <int MODE, bool LHALF>
+__device__ __forceinline__ bool integrate_particle(const SimParams &P, const Ptrs &D, DevCtl *ctl, int i, float4 pi,
+                                                   float4 vi, float fx, float fy, float fz, uint32_t par,
+                                                   uint32_t opar, unsigned long long step0, int out_fout)
+{
+    bool moved = false;
     if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&ctl->err, kErrNonFinite);
     const uint32_t nx = par ^ 1u;
     if (MODE == kForceEval) {
@@ -183,6 +188,17 @@ __device__ __forceinline__ bool force_epilogue(const SimParams &P, const Ptrs &D
     return moved;
 }
 
+// Epilogue of the force kernels for particle i: bonds, body force, then the
+// final stage (integrate_particle).
+template <int MODE, bool LHALF>
+__device__ __forceinline__ bool force_epilogue(const SimParams &P, const Ptrs &D, DevCtl *ctl, int i, float4 pi,
+                                               float4 vi, float fx, float fy, float fz, uint32_t par, uint32_t opar,
+                                               unsigned long long step0, int out_fout)
+{
+    add_bonds_body(P, D, i, pi, D.pos[par], opar, fx, fy, fz);
+    return integrate_particle<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout);
+}
+
 // ---------------------------------------------------------------------------
 // Fused pair force.  Each warp owns 32 consecutive particles (cell order) and
 // walks their neighbour rows in lockstep, reading the k-th entry of all 32
@@ -215,12 +231,20 @@ __device__ __forceinline__ float3 pair_delta(const SimParams &P, float4 pj, floa
     return make_float3(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
 }
 
-template <bool ONE_SPECIES, int SMODE, bool WRAP>
+// Vector reduction into global memory (sm_90+): adds (x, y, z, 0) to *p.
+__device__ __forceinline__ void red_add_f4(float4 *p, float x, float y, float z)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(0.0f)
+                 : "memory");
+}
+
+template <bool ONE_SPECIES, int SMODE, bool WRAP, bool N3>
 __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__restrict__ pos,
                                            const float4 *__restrict__ vel, const uint32_t *__restrict__ row,
                                            int cnt, int maxcnt, uint32_t self, uint32_t own_idx, float4 pi,
                                            int lane, float4 (*s_q)[kQueue], uint8_t (*s_qo)[kQueue],
-                                           float (*s_acc)[3][32], const float *a_tab, int warp)
+                                           float (*s_acc)[3][32], const float *a_tab, int warp,
+                                           float4 *facc)
 {
     const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -262,6 +286,8 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             fx = sc * dx;
             fy = sc * dy;
             fz = sc * dz;
+            // Newton's third law: the partner (a later row) gets -F once
+            if (N3) red_add_f4(facc + __float_as_uint(q.w), -fx, -fy, -fz);
         }
         // per-owner sums in lane order; the lowest lane of each group adds
         const uint32_t grp = __match_any_sync(0xFFFFFFFFu, owner);
@@ -336,7 +362,7 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
     }
 }
 
-template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF>
+template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF, bool N3>
 __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, int out_fout)
 {
     constexpr int W = kForceThreads / 32;
@@ -375,19 +401,49 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     const bool all_interior = __all_sync(0xFFFFFFFFu, interior) && P.wrap_margin > 0.0f;
     __syncwarp();
     if (all_interior)
-        warp_pairs<ONE_SPECIES, SMODE, false>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
-                                                     s_acc, a_tab, warp);
+        warp_pairs<ONE_SPECIES, SMODE, false, N3>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
+                                                  s_acc, a_tab, warp, D.facc);
     else
-        warp_pairs<ONE_SPECIES, SMODE, true>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
-                                                    s_acc, a_tab, warp);
+        warp_pairs<ONE_SPECIES, SMODE, true, N3>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
+                                                 s_acc, a_tab, warp, D.facc);
     float fx = s_acc[warp][0][lane], fy = s_acc[warp][1][lane], fz = s_acc[warp][2][lane];
 
+    if (N3) {
+        // this row's share of particle i's force; the settle kernel adds the
+        // shares other rows pushed into facc and completes the mode
+        if (valid) {
+            add_bonds_body(P, D, i, pi, pos, opar, fx, fy, fz);
+            D.fown[i] = make_float4(fx, fy, fz, 0.0f);
+        }
+        return;
+    }
     bool moved = false;
     if (valid)
         moved = force_epilogue<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout);
-    if (MODE != kForceEval) {
-        finish_block(P, ctl, moved, true, MODE == kForceStep);
+    if (MODE != kForceEval) finish_block(ctl, moved);
+}
+
+// Newton-3 mode: f_i = own row share + the shares other rows added, then
+// the force mode's final stage (store, or integrate into the other set).
+// Clears facc for the next evaluation.
+template <int MODE, bool LHALF>
+__global__ void __launch_bounds__(kThreads) k_settle(SimParams P, Ptrs D, int out_fout)
+{
+    DevCtl *ctl = D.ctl;
+    const uint32_t par = ctl->parity;
+    const uint32_t opar = ctl->oparity;
+    const unsigned long long step0 = ctl->step;
+    bool moved = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const float4 a = D.fown[i];
+        const float4 b = D.facc[i];
+        D.facc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 pi = D.pos[par][i];
+        const float4 vi = D.vel[par][i];
+        moved |= integrate_particle<MODE, LHALF>(P, D, ctl, i, pi, vi, a.x + b.x, a.y + b.y, a.z + b.z, par, opar,
+                                                 step0, out_fout);
     }
+    if (MODE != kForceEval) finish_block(ctl, moved);
 }
 
 
@@ -523,15 +579,15 @@ int grid_for(int n)
 
 constexpr int kMaxDynSmem = 160 * 1024;  // largest staging buffer the brick builder accepts
 
-template <bool ONE, int MODE, bool LH>
+template <bool ONE, int MODE, bool LH, bool N3>
 cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream_t s)
 {
     const int g = (P.n + kForceThreads - 1) / kForceThreads;
     switch (P.s_mode) {
-    case 1: k_force<ONE, 1, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
-    case 2: k_force<ONE, 2, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
-    case 3: k_force<ONE, 3, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
-    default: k_force<ONE, 0, MODE, LH><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 1: k_force<ONE, 1, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 2: k_force<ONE, 2, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 3: k_force<ONE, 3, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    default: k_force<ONE, 0, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
     }
     return cudaGetLastError();
 }
@@ -539,13 +595,35 @@ cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream
 template <bool ONE>
 cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, cudaStream_t s)
 {
-    if (mode == kForceEval) return launch_force_m<ONE, kForceEval, true>(P, D, of, s);
-    if (P.lambda_half) {
-        if (mode == kForceStep) return launch_force_m<ONE, kForceStep, true>(P, D, of, s);
-        return launch_force_m<ONE, kForceFinish, true>(P, D, of, s);
+    if (P.newton3) {
+        // pair kernel (accumulation only), then the settle kernel of the mode
+        cudaError_t e = launch_force_m<ONE, kForceEval, true, true>(P, D, of, s);
+        if (e != cudaSuccess) return e;
+        // one thread per particle: the kernel streams memory and needs every
+        // load in flight at once
+        const int g = (P.n + kThreads - 1) / kThreads;
+        if (mode == kForceEval) k_settle<kForceEval, true><<<g, kThreads, 0, s>>>(P, D, of);
+        else if (P.lambda_half) {
+            if (mode == kForceStep) k_settle<kForceStep, true><<<g, kThreads, 0, s>>>(P, D, of);
+            else k_settle<kForceFinish, true><<<g, kThreads, 0, s>>>(P, D, of);
+        } else {
+            if (mode == kForceStep) k_settle<kForceStep, false><<<g, kThreads, 0, s>>>(P, D, of);
+            else k_settle<kForceFinish, false><<<g, kThreads, 0, s>>>(P, D, of);
+        }
+    } else {
+        cudaError_t e;
+        if (mode == kForceEval) e = launch_force_m<ONE, kForceEval, true, false>(P, D, of, s);
+        else if (P.lambda_half)
+            e = mode == kForceStep ? launch_force_m<ONE, kForceStep, true, false>(P, D, of, s)
+                                   : launch_force_m<ONE, kForceFinish, true, false>(P, D, of, s);
+        else
+            e = mode == kForceStep ? launch_force_m<ONE, kForceStep, false, false>(P, D, of, s)
+                                   : launch_force_m<ONE, kForceFinish, false, false>(P, D, of, s);
+        if (e != cudaSuccess) return e;
     }
-    if (mode == kForceStep) return launch_force_m<ONE, kForceStep, false>(P, D, of, s);
-    return launch_force_m<ONE, kForceFinish, false>(P, D, of, s);
+    if (mode == kForceStep) k_advance<true, true><<<1, 1, 0, s>>>(P, D);
+    else if (mode == kForceFinish) k_advance<true, false><<<1, 1, 0, s>>>(P, D);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -566,10 +644,12 @@ cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s)
 
 cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s)
 {
+    const int g = (P.n + kThreads - 1) / kThreads;
     if (P.lambda_half)
-        k_phase1<true><<<grid_for(P.n), kThreads, 0, s>>>(P, D);
+        k_phase1<true><<<g, kThreads, 0, s>>>(P, D);
     else
-        k_phase1<false><<<grid_for(P.n), kThreads, 0, s>>>(P, D);
+        k_phase1<false><<<g, kThreads, 0, s>>>(P, D);
+    k_advance<false, true><<<1, 1, 0, s>>>(P, D);
     return cudaGetLastError();
 }
 

@@ -248,7 +248,7 @@ __global__ void k_nbuild(SimParams P, Ptrs D)
             if (cc == kNone) break;
             uint32_t b = D.cell_start[cc], e = D.cell_start[cc + 1];
             for (uint32_t j = b; j < e; ++j) {
-                if (j == (uint32_t)i) continue;
+                if (P.newton3 ? j <= (uint32_t)i : j == (uint32_t)i) continue;
                 float4 pj = pos[j];
                 float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
                 float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
@@ -271,7 +271,9 @@ __global__ void k_nbuild(SimParams P, Ptrs D)
     if ((threadIdx.x & 31) == 0) atomicMax(&D.ctl->max_nnb, local_max);
 }
 
-// Neighbour build, one CTA per brick (see brick.cuh).  The CTA stages the
+// Neighbour build, one CTA per brick (see brick.cuh).  In Newton-3 mode the
+// rows keep only partners j > i (half rows), and stencil cells whose
+// particles all precede i are skipped outright.  The CTA stages the
 // positions of the brick's halo in shared memory with bulk (TMA) copies; each
 // thread owns one particle of the brick and tests the particles of its 27
 // surrounding cells, read from shared memory, with the FP32 predicate,
@@ -316,7 +318,7 @@ __device__ __forceinline__ float slab_gap(float f, int o, float side)
 // predicate, as 32-bit global indices in the particle's row of its 32-wide
 // tile (entry k at k * 32).  Candidate positions come from the staged halo
 // (STAGED) or from global memory.
-template <bool WRAP, bool STAGED>
+template <bool WRAP, bool STAGED, bool HALF>
 __device__ __forceinline__ uint32_t build_row(const SimParams &P, const float4 *pos, const float4 *s_pos,
                                               const uint32_t *s_off, const uint32_t *s_gstart,
                                               const uint32_t *s_cnt, int hx, int hy, int hz, const float *frac,
@@ -332,10 +334,11 @@ __device__ __forceinline__ uint32_t build_row(const SimParams &P, const float4 *
                 if (gyz + slab_gap(frac[0], ox, side[0]) >= P.rlist2) continue;
                 const int t = brick_halo_slot(hx + ox, hy + oy, hz + oz);
                 const uint32_t o = s_off[t], g = s_gstart[t], n = s_cnt[t];
+                if (HALF && g + n <= i + 1u) continue;  // every particle of the cell precedes i
                 for (uint32_t e = 0; e < n; ++e) {
                     const uint32_t j = g + e;
                     const float4 pj = STAGED ? s_pos[o + e] : pos[j];
-                    const bool hit = within_list<WRAP>(P, pj, pi) & (j != i);
+                    const bool hit = within_list<WRAP>(P, pj, pi) & (HALF ? (j > i) : (j != i));
                     if (hit & (cnt < cap)) row[(size_t)cnt * 32] = j;
                     cnt += hit ? 1u : 0u;
                 }
@@ -394,11 +397,21 @@ __global__ void __launch_bounds__(kBuildThreads) k_nbuild_brick(SimParams P, Ptr
         uint32_t *row = D.nbr + (size_t)(i >> 5) * cap * 32 + (i & 31u);
         const float frac[3] = {fx_, fy_, fz_};
         uint32_t cnt;
-        if (local)
-            cnt = warp_inner ? build_row<false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap)
-                             : build_row<true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
-        else
-            cnt = build_row<true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+        if (P.newton3) {
+            if (local)
+                cnt = warp_inner
+                          ? build_row<false, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap)
+                          : build_row<true, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+            else
+                cnt = build_row<true, false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+        } else {
+            if (local)
+                cnt = warp_inner
+                          ? build_row<false, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap)
+                          : build_row<true, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+            else
+                cnt = build_row<true, false, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+        }
         if (cnt > cap) atomicOr(&D.ctl->err, kErrNbrOverflow);
         D.nnb[i] = min(cnt, cap);
         local_max = max(local_max, cnt);

@@ -87,7 +87,7 @@ def test_deterministic_runs():
     st = workloads.make("fluid_small")
     outs = []
     for _ in range(2):
-        g, _ = make_pair(st["cfg"])
+        g, _ = make_pair(st["cfg"], deterministic=1)
         g.set_state(st["x"], st["v"])
         g.step(57)
         outs.append(g.state())
@@ -113,3 +113,18 @@ def test_checkpoint_resume():
     # the lists differ in build time, so sums differ in rounding order only
     assert np.abs(xa - xb).max() < 1e-5
     assert np.abs(va - vb).max() < 1e-3
+
+
+def test_newton3_and_deterministic_modes_agree():
+    """One evaluation per pair with atomics for the partner, against every pair
+    evaluated from both sides in fixed order: same forces within rounding, and
+    the same trajectory over a few steps."""
+    st = workloads.make("fluid_small")
+    a, _ = make_pair(st["cfg"], deterministic=0)
+    b, _ = make_pair(st["cfg"], deterministic=1)
+    a.set_state(st["x"], st["v"], step=4)
+    b.set_state(st["x"], st["v"], step=4)
+    assert force_error(a.forces(), b.forces())[0] < 1e-6
+    a.step(5)
+    b.step(5)
+    assert np.abs(a.state()[0] - b.state()[0]).max() < 1e-5

@@ -50,10 +50,11 @@ def test_pair_rng_extreme_words():
 ALL = ["fluid_small", "poiseuille_small", "amphiphile_small", "dense_small", "tiny_box"]
 
 
+@pytest.mark.parametrize("deterministic", [0, 1])
 @pytest.mark.parametrize("name", ALL)
-def test_neighbors_bit_exact(name):
+def test_neighbors_bit_exact(name, deterministic):
     st, cfg, box, bonds = _workload(name)
-    g, o = make_pair(cfg, box=box)
+    g, o = make_pair(cfg, box=box, deterministic=deterministic)
     g.set_state(st["x"], st["v"], st["species"])
     x32, _, _ = g.state()
     rl = cfg["rc"] + 0.3
@@ -88,10 +89,11 @@ def _workload(name):
     raise KeyError(name)
 
 
+@pytest.mark.parametrize("deterministic", [0, 1])
 @pytest.mark.parametrize("name", ALL)
-def test_forces_match_oracle(name):
+def test_forces_match_oracle(name, deterministic):
     st, cfg, box, bonds = _workload(name)
-    g, o = make_pair(cfg, box=box, bonds=bonds)
+    g, o = make_pair(cfg, box=box, bonds=bonds, deterministic=deterministic)
     g.set_state(st["x"], st["v"], st["species"], step=17)
     if bonds is not None:
         g.set_bonds(bonds, cfg["k_bond"], cfg["r0_bond"])
@@ -101,8 +103,12 @@ def test_forces_match_oracle(name):
     fg = g.forces()
     err, rms = force_error(fg, fo)
     assert err < FORCE_TOL, (err, rms)
-    # the integrator's stored force is the same evaluation
-    assert np.abs(g.force() - fg).max() == 0.0
+    # the integrator's stored force is the same evaluation (bit-identical
+    # when sums run in a fixed order)
+    if deterministic:
+        assert np.abs(g.force() - fg).max() == 0.0
+    else:
+        assert force_error(g.force(), fg)[0] < 1e-6
 
 
 def test_observables_match_oracle():
