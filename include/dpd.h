@@ -42,7 +42,7 @@ typedef enum {
     DPD_ERR_ARG = 1,          /* invalid argument; nothing changed */
     DPD_ERR_OOM = 2,          /* device or host allocation failed */
     DPD_ERR_CUDA = 3,         /* a CUDA call failed (latched) */
-    DPD_ERR_NBR_OVERFLOW = 4, /* a particle had more neighbours than the list holds */
+    DPD_ERR_NBR_OVERFLOW = 4, /* a group of 32 particles had more pairs than its list holds */
     DPD_ERR_NONFINITE = 5,    /* a force or position became NaN / Inf */
     DPD_ERR_TIMEOUT = 6,      /* the GPU did not finish within the wait limit */
     DPD_ERR_STATE = 7         /* call order: e.g. dpd_step before dpd_set_state */
@@ -59,7 +59,10 @@ typedef struct {
     uint64_t seed;            /* global seed of the random force (default 42) */
     double lambda;            /* velocity-Verlet prediction factor (default 0.5) */
     double body_force[3];     /* g (force per particle, unit mass) */
-    int32_t nbr_capacity;     /* neighbours per particle; 0 = from density */
+    int32_t nbr_capacity;     /* list capacity per particle: particles are listed in
+                                 groups of 32 consecutive ones, each group holding
+                                 up to 32 x nbr_capacity pair entries; 0 = from the
+                                 density, grown when a build overflows */
     int32_t graph_steps;      /* steps per captured CUDA graph (default 8; 0 = no graphs) */
     int32_t deterministic;    /* 0 (default): each pair is evaluated once and its force is
                                  added to the second particle with float atomics, so force
@@ -100,7 +103,8 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
                       double gamma, double kT, double rc, double s, double dt,
                       const dpd_options *opt);
 
-/* Load particles (Alg. 1 "CPU -> GPU").  x, v: n x 3; positions are wrapped
+/* Load particles (Alg. 1 "CPU -> GPU").  1 <= n <= 2^27 (a list entry packs
+ * a particle index into 27 bits).  x, v: n x 3; positions are wrapped
  * into [0, L) and rounded to FP32 on the device.  species: n entries in
  * [0, n_species) or NULL (all 0).  tag: n distinct identity tags keying the
  * random force, or NULL (tag = particle index).  step: the step number of

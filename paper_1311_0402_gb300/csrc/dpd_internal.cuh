@@ -12,10 +12,15 @@
 //   force[p] float4 (fx, fy, fz, 0)                       16 B
 //   tag[p]   u32 identity tag (keys the random force)
 //   pid[p]   u32 caller's particle index
-// Neighbour list: tiles of 32 particles, column-major inside a tile
-// (nbr[(p/32)*cap*32 + k*32 + p%32]), so a warp reading its k-th
-// neighbours issues one 128-byte transaction (the transposed layout of
-// Sec. 3.3, written directly).
+// Neighbour list, packed per group: a group is a run of at most 32
+// consecutive particles (the particles of one brick in 32s, or 32-aligned
+// tiles when there are no bricks).  Group g's pairs are one dense run of
+// 32-bit entries at nbr[g * gcap], entry = (owner lane << 27) | j for the
+// pair of particle first + lane with particle j; gdesc[g] = (first,
+// owners | entries << 6).  A warp reads 32 consecutive entries in one
+// 128-byte transaction (the coalesced, transposed access of Sec. 3.3), and
+// the work of a group follows its total pair count rather than its longest
+// row.
 #pragma once
 
 #include <cstdint>
@@ -26,6 +31,10 @@ namespace dpd {
 constexpr int kMaxSpecies = 8;
 constexpr int kMaxBonds = 6;          // bonds per particle
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kOwnerShift = 27;                       // list entry: owner lane above bit 27
+constexpr uint32_t kIndexMask = (1u << kOwnerShift) - 1u;
+constexpr int64_t kMaxParticles = int64_t(1) << kOwnerShift;
+constexpr int kGroup = 32;                            // particles per group (one warp)
 constexpr int kStencil = 27;
 // bricks: aligned kBrick^3 blocks of cells (contiguous ranges of the Morton
 // cell order) with a one-cell halo, staged in shared memory by the builder
@@ -45,7 +54,7 @@ struct DevCtl {
     uint32_t since_rebuild;  // steps since the last rebuild
     unsigned long long step; // step number of the live state
     unsigned long long nrebuild;
-    uint32_t max_nnb;        // largest neighbour count of the last build
+    uint32_t max_nnb;        // largest group list total (pair entries) of the last build
     uint32_t rebuild_next;   // displacement flag raised by the kernel running now
     uint32_t pad0;
     uint32_t oparity;        // live set of the order arrays (tag, pid): flips only at a rebuild
@@ -55,7 +64,9 @@ struct SimParams {
     int n;
     int ncell;
     int nc[3];
-    int cap;                  // neighbour capacity per particle
+    int cap;                  // neighbour capacity per particle (a group holds 32 x cap entries)
+    int gcap;                 // entries per group list = 32 * cap
+    int ngroups;              // group descriptors (lists) in use
     float L[3];
     float halfL[3];
     float cells_per_len[3];   // nc / L
@@ -105,11 +116,12 @@ struct Ptrs {
     uint32_t *perm;                // [n] new position -> old position
     uint32_t *idx_of_pid;          // [n] caller index -> current position
     // neighbours
-    uint32_t *nbr;                 // tiled list
-    uint32_t *nnb;                 // [n] counts
+    uint32_t *nbr;                 // packed group lists, [ngroups][gcap]
+    uint2 *gdesc;                  // [ngroups] (first particle, owners | entries << 6)
     // bricks
     const uint32_t *brick_rank_lo; // [nbricks] first Morton rank of the brick's cells
     const uint32_t *brick_rank_hi; // [nbricks] last Morton rank (inclusive)
+    const uint32_t *brick_ord;     // [nbricks] position of the brick in ascending rank order
     // bonds
     const uint32_t *bond_partner;  // [n][kMaxBonds] partner caller indices
     // reductions

@@ -34,6 +34,7 @@ struct Geometry {
     std::vector<uint32_t> stencil;       // [ncell][27]
     int nb[3] = {0, 0, 0};               // bricks per axis
     std::vector<uint32_t> brick_lo, brick_hi;  // first / last Morton rank of each brick
+    std::vector<uint32_t> brick_ord;           // position of each brick in ascending rank order
 };
 
 uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
@@ -102,6 +103,13 @@ void build_geometry(const int nc[3], Geometry &g)
                 g.brick_lo[b] = std::min(g.brick_lo[b], r);
                 g.brick_hi[b] = std::max(g.brick_hi[b], r);
             }
+    // the bricks partition the rank range into consecutive intervals; their
+    // order along it numbers the group lists
+    std::vector<std::pair<uint32_t, int>> by_rank(nbricks);
+    for (int b = 0; b < nbricks; ++b) by_rank[b] = {g.brick_lo[b], b};
+    std::sort(by_rank.begin(), by_rank.end());
+    g.brick_ord.assign(nbricks, 0u);
+    for (int k = 0; k < nbricks; ++k) g.brick_ord[by_rank[k].second] = (uint32_t)k;
 }
 
 }  // namespace
@@ -204,7 +212,8 @@ dpd_status check_err(dpd_sim *h, DevCtl &c)
     if (st) return st;
     if (c.err & kErrNbrOverflow)
         return fail(h, DPD_ERR_NBR_OVERFLOW,
-                    "neighbour list overflow: " + std::to_string(c.max_nnb) + " > capacity " + std::to_string(h->P.cap));
+                    "neighbour list overflow: a group list of " + std::to_string(c.max_nnb) + " entries > capacity " +
+                        std::to_string(h->P.gcap));
     if (c.err & kErrNonFinite) return fail(h, DPD_ERR_NONFINITE, "non-finite force");
     if (c.err & kErrTimeout) return fail(h, DPD_ERR_TIMEOUT, "a device-side wait for staged data ran out");
     return DPD_OK;
@@ -284,8 +293,20 @@ dpd_status get_graph(dpd_sim *h, int k, cudaGraphExec_t *out)
     return DPD_OK;
 }
 
-// Row tiles of 32 consecutive particles.
-size_t row_tiles(const dpd_sim *, int64_t n) { return (size_t)(n + 31) / 32; }
+// Group lists: with bricks, brick b's groups take ids from lo_b / 32 +
+// ord(b), so n / 32 + nbricks ids cover every brick; otherwise 32-aligned
+// tiles.
+int group_count(const dpd_sim *h, int64_t n)
+{
+    return h->P.use_bricks ? (int)(n / kGroup) + h->P.nbricks : (int)((n + kGroup - 1) / kGroup);
+}
+
+// per-particle capacity from the largest group total of a build
+int capacity_for_total(uint32_t max_total)
+{
+    int cap = (int)(((uint64_t)max_total * 5 / 4 + 64 + kGroup - 1) / kGroup);
+    return std::max((cap + 7) / 8 * 8, 32);
+}
 
 int auto_capacity(const dpd_sim *h, int64_t n)
 {
@@ -324,16 +345,18 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     A((void **)&D.skey, sizeof(unsigned long long) * (size_t)n);
     A((void **)&D.perm, u4);
     A((void **)&D.idx_of_pid, u4);
-    A((void **)&D.nnb, u4);
-    A((void **)&D.nbr, row_tiles(h, n) * 32 * (size_t)cap * sizeof(uint32_t));
+    h->P.ngroups = group_count(h, n);
+    A((void **)&D.gdesc, sizeof(uint2) * (size_t)h->P.ngroups);
+    A((void **)&D.nbr, (size_t)h->P.ngroups * kGroup * (size_t)cap * sizeof(uint32_t));
     h->red_doubles = std::max<size_t>((size_t)observe_blocks_for((int)n) * 8, 4096);
     A((void **)&D.red, h->red_doubles * sizeof(double));
     A((void **)&D.bond_partner, sizeof(uint32_t) * (size_t)n * kMaxBonds);
     if (st) return st;
     CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(D.nnb, 0, u4, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(D.gdesc, 0, sizeof(uint2) * (size_t)h->P.ngroups, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(D.facc, 0, f4, h->stream));
     h->P.cap = cap;
+    h->P.gcap = kGroup * cap;
     h->cap_alloc_n = n;
     return DPD_OK;
 }
@@ -351,12 +374,16 @@ dpd_status rebuild_and_force(dpd_sim *h, bool grow_on_overflow)
         dpd_status st = check_err(h, c);
         if (st != DPD_ERR_NBR_OVERFLOW || !grow_on_overflow) return st;
         // grow the list: keep the particle arrays, reallocate the table
-        int cap = (int)((c.max_nnb * 5 / 4 + 16 + 7) / 8 * 8);
+        const int cap = capacity_for_total(c.max_nnb);
+        if ((int64_t)cap * kGroup >= (int64_t(1) << 26))
+            return fail(h, DPD_ERR_NBR_OVERFLOW, "neighbour list overflow: group list beyond 2^26 entries");
         cudaFree(h->D.nbr);
         h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->D.nbr));
-        st = dev_alloc(h, (void **)&h->D.nbr, row_tiles(h, h->n) * 32 * (size_t)cap * sizeof(uint32_t), h->allocs);
+        st = dev_alloc(h, (void **)&h->D.nbr, (size_t)h->P.ngroups * kGroup * (size_t)cap * sizeof(uint32_t),
+                       h->allocs);
         if (st) return st;
         h->P.cap = cap;
+        h->P.gcap = kGroup * cap;
         drop_graphs(h);
     }
     return fail(h, DPD_ERR_NBR_OVERFLOW, "neighbour list overflow after regrowing");
@@ -529,6 +556,7 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     A((void **)&h->D.scan_part, sizeof(uint32_t) * (h->n_scan_blocks + 1));
     A((void **)&h->D.brick_rank_lo, sizeof(uint32_t) * P.nbricks);
     A((void **)&h->D.brick_rank_hi, sizeof(uint32_t) * P.nbricks);
+    A((void **)&h->D.brick_ord, sizeof(uint32_t) * P.nbricks);
 
     if (st) {
         std::string m = h->err;
@@ -546,6 +574,9 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     if (e == cudaSuccess)
         e = cudaMemcpyAsync((void *)h->D.brick_rank_hi, h->geo.brick_hi.data(), sizeof(uint32_t) * P.nbricks,
                             cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)h->D.brick_ord, h->geo.brick_ord.data(), sizeof(uint32_t) * P.nbricks,
+                            cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->D.cell_count, 0, sizeof(uint32_t) * P.ncell, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->D.ctl, 0, sizeof(DevCtl), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -562,7 +593,7 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
 {
     dpd_status st = guard(h, false);
     if (st) return st;
-    if (n <= 0 || n >= (int64_t)1 << 31 || !x || !v) return fail(h, DPD_ERR_ARG, "need 0 < n < 2^31 and x, v");
+    if (n <= 0 || n > kMaxParticles || !x || !v) return fail(h, DPD_ERR_ARG, "need 0 < n <= 2^27 and x, v");
     std::vector<float4> pos(n), vel(n);
     std::vector<uint32_t> tg(n), pid(n);
     for (int64_t i = 0; i < n; ++i) {
@@ -677,19 +708,24 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
     st = read_ctl(h, c);
     if (st) return st;
     const int64_t n = h->n;
-    const size_t tiles = row_tiles(h, n);
-    std::vector<uint32_t> nbr(tiles * 32 * (size_t)h->P.cap), nnb(n), pid(n);
+    const int G = h->P.ngroups;
+    std::vector<uint32_t> nbr((size_t)G * h->P.gcap), pid(n);
+    std::vector<uint2> desc(G);
     CUDA_TRY(h, cudaMemcpyAsync(nbr.data(), h->D.nbr, sizeof(uint32_t) * nbr.size(), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(nnb.data(), h->D.nnb, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(desc.data(), h->D.gdesc, sizeof(uint2) * G, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.oparity], sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
     st = wait(h);
     if (st) return st;
     std::vector<uint64_t> pr;
-    for (int64_t i = 0; i < n; ++i) {
-        const uint32_t *row = nbr.data() + (size_t)(i >> 5) * h->P.cap * 32 + (i & 31);
-        for (uint32_t k = 0; k < nnb[i]; ++k) {
-            const uint32_t j = row[(size_t)k * 32];
-            if (j >= (uint32_t)n) return fail(h, DPD_ERR_STATE, "neighbour index out of range");
+    for (int g = 0; g < G; ++g) {
+        const uint32_t first = desc[g].x, owners = desc[g].y & 63u, ne = desc[g].y >> 6;
+        if (owners > (uint32_t)kGroup || ne > (uint32_t)h->P.gcap || (owners && first + owners > (uint64_t)n))
+            return fail(h, DPD_ERR_STATE, "corrupt group descriptor");
+        const uint32_t *list = nbr.data() + (size_t)g * h->P.gcap;
+        for (uint32_t k = 0; k < ne; ++k) {
+            const uint32_t own = list[k] >> kOwnerShift, j = list[k] & kIndexMask;
+            if (own >= owners || j >= (uint32_t)n) return fail(h, DPD_ERR_STATE, "neighbour entry out of range");
+            const uint32_t i = first + own;
             const uint32_t a = std::min(pid[i], pid[j]), b2 = std::max(pid[i], pid[j]);
             if (a != b2) pr.push_back(((uint64_t)a << 32) | b2);
         }

@@ -75,20 +75,22 @@ __global__ void k_phase1(SimParams P, Ptrs D)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const float4 f = frc[i];
         const float4 v = vel[i];
+        const uint32_t tg = tag[i];
+        const float4 xr = D.xref[i];
         const float ux = fmaf(P.half_dt, f.x, v.x), uy = fmaf(P.half_dt, f.y, v.y), uz = fmaf(P.half_dt, f.z, v.z);
         float4 x = pos[i];
         x.x = wrap_pos(fmaf(P.dt, ux, x.x), P.L[0], invL[0]);
         x.y = wrap_pos(fmaf(P.dt, uy, x.y), P.L[1], invL[1]);
         x.z = wrap_pos(fmaf(P.dt, uz, x.z), P.L[2], invL[2]);
         pos[i] = x;
-        const float sig = __uint_as_float(signature(tag[i], step1, P.key));
+        const float sig = __uint_as_float(signature(tg, step1, P.key));
         if (LHALF) {
             vel[i] = make_float4(ux, uy, uz, sig);
         } else {
             vel[i] = make_float4(fmaf(P.lambda_dt, f.x, v.x), fmaf(P.lambda_dt, f.y, v.y), fmaf(P.lambda_dt, f.z, v.z), sig);
             D.vkick[par][i] = make_float4(ux, uy, uz, 0.0f);
         }
-        moved |= moved_beyond(P, x, D.xref[i]);
+        moved |= moved_beyond(P, x, xr);
     }
     finish_block(ctl, moved);
 }
@@ -150,6 +152,16 @@ __device__ __forceinline__ bool integrate_particle(const SimParams &P, const Ptr
                                                    uint32_t opar, unsigned long long step0, int out_fout)
 {
     bool moved = false;
+    // every input is read before the first store: as far as the compiler
+    // knows the stores may alias them, and reads issued after a store would
+    // wait for another round trip to memory
+    float4 u = vi, xr = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t tg = 0;
+    if (MODE != kForceEval && !LHALF) u = D.vkick[par][i];
+    if (MODE == kForceStep) {
+        tg = D.tag[opar][i];
+        xr = D.xref[i];
+    }
     if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(&ctl->err, kErrNonFinite);
     const uint32_t nx = par ^ 1u;
     if (MODE == kForceEval) {
@@ -157,7 +169,6 @@ __device__ __forceinline__ bool integrate_particle(const SimParams &P, const Ptr
         out[i] = make_float4(fx, fy, fz, 0.0f);
     } else if (MODE == kForceFinish) {
         // phase 2: v = u + dt/2 f; the state at the full step goes to the other set
-        const float4 u = LHALF ? vi : D.vkick[par][i];
         D.vel[nx][i] = make_float4(fmaf(P.half_dt, fx, u.x), fmaf(P.half_dt, fy, u.y), fmaf(P.half_dt, fz, u.z), vi.w);
         D.pos[nx][i] = pi;
         D.force[nx][i] = make_float4(fx, fy, fz, 0.0f);
@@ -165,7 +176,6 @@ __device__ __forceinline__ bool integrate_particle(const SimParams &P, const Ptr
     } else {
         // phase 2 of this step and phase 1 of the next:
         //   v = u + dt/2 f;  u' = v + dt/2 f;  v~ = v + lambda dt f;  x' = x + dt u'
-        const float4 u = LHALF ? vi : D.vkick[par][i];
         float ux, uy, uz, tx, ty, tz;
         if (LHALF) {
             ux = fmaf(P.dt, fx, u.x); uy = fmaf(P.dt, fy, u.y); uz = fmaf(P.dt, fz, u.z);
@@ -181,9 +191,9 @@ __device__ __forceinline__ bool integrate_particle(const SimParams &P, const Ptr
         x.y = wrap_pos(fmaf(P.dt, uy, x.y), P.L[1], 1.0f / P.L[1]);
         x.z = wrap_pos(fmaf(P.dt, uz, x.z), P.L[2], 1.0f / P.L[2]);
         D.pos[nx][i] = x;
-        const uint32_t sig = signature(D.tag[opar][i], (uint32_t)(step0 + 2ull), P.key);
+        const uint32_t sig = signature(tg, (uint32_t)(step0 + 2ull), P.key);
         D.vel[nx][i] = make_float4(tx, ty, tz, __uint_as_float(sig));
-        moved = moved_beyond(P, x, D.xref[i]);
+        moved = moved_beyond(P, x, xr);
     }
     return moved;
 }
@@ -200,20 +210,23 @@ __device__ __forceinline__ bool force_epilogue(const SimParams &P, const Ptrs &D
 }
 
 // ---------------------------------------------------------------------------
-// Fused pair force.  Each warp owns 32 consecutive particles (cell order) and
-// walks their neighbour rows in lockstep, reading the k-th entry of all 32
-// rows in one coalesced load.  Pairs inside r_c (the FP32 predicate) are
-// appended to a per-warp ring queue in shared memory in (k, lane) order (a
-// ballot gives each hit its slot, as the paper's builder does for list
-// entries); every time 32 are queued the whole warp evaluates them together,
-// one pair per lane, so the hash / Box-Muller / force arithmetic runs with
-// full warps whatever the hit pattern.  The 32 results are summed per owning
-// particle in lane order (match-any groups, shuffles) and added to the
-// owner's shared accumulator: the summation order is fixed, the result
-// deterministic.  Every pair is evaluated for both of its particles (full
-// rows), so no thread writes another particle's force.
+// Fused pair force.  Each warp owns one group (at most 32 consecutive
+// particles in cell order, lane = owner) and walks the group's packed list
+// 32 entries at a time: one coalesced load, every lane a candidate pair
+// (owner, j).  Pairs inside r_c (the FP32 predicate) are appended to a
+// per-warp ring queue in shared memory in list order (a ballot gives each
+// hit its slot, as the paper's builder does for list entries); every time 32
+// are queued the whole warp evaluates them together, one pair per lane, so
+// the hash / Box-Muller / force arithmetic runs with full warps whatever the
+// hit pattern.
 //   F = a_{t_i t_j} w - gamma w_R^2 (e . v_ij) + sigma/sqrt(dt) w_R xi_ij,
 //   f_i += F e_ij,  e_ij = (x_i - x_j) / r.
+// The 32 results of a batch are summed per owner by a segmented scan and
+// added to the owners' shared accumulators.  Deterministic mode (full lists,
+// each pair seen from both sides): the adds run in lane order, so every
+// force is summed in a fixed order.  Newton-3 mode (half lists): the adds
+// are shared-memory atomics, and the partner's share, -F e_ij, goes to
+// facc[j] by a global vector reduction.
 // The epilogue adds bonds and the body force and, per MODE, writes the force
 // or integrates (see launch_force).
 constexpr int kQueue = 64;  // ring slots per warp (< 32 pending + 32 new)
@@ -238,97 +251,115 @@ __device__ __forceinline__ void red_add_f4(float4 *p, float x, float y, float z)
                  : "memory");
 }
 
+// Shared state of a warp: owners' positions and velocities, the queue and
+// the owners' force accumulators.
+struct WarpSmem {
+    float4 pi[32];
+    float4 vi[32];
+    float4 q[kQueue];      // (d, j)
+    uint8_t qo[kQueue];    // owner lane | partner species << 5
+    float acc[3][32];
+};
+
 template <bool ONE_SPECIES, int SMODE, bool WRAP, bool N3>
 __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__restrict__ pos,
-                                           const float4 *__restrict__ vel, const uint32_t *__restrict__ row,
-                                           int cnt, int maxcnt, uint32_t self, uint32_t own_idx, float4 pi,
-                                           int lane, float4 (*s_q)[kQueue], uint8_t (*s_qo)[kQueue],
-                                           float (*s_acc)[3][32], const float *a_tab, int warp,
-                                           float4 *facc)
+                                           const float4 *__restrict__ vel, const uint32_t *__restrict__ list,
+                                           uint32_t nent, int lane, WarpSmem &w, const float *a_tab, float4 *facc)
 {
     const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
     const uint32_t lt_mask = (1u << lane) - 1u;
 
     // Evaluate queue entries [head, head + nb) (nb <= 32), one per lane, and
-    // add each owner's sum to its accumulator.
+    // add each result to its owner's accumulator.
     auto run_batch = [&](uint32_t head, int nb) {
         float fx = 0.f, fy = 0.f, fz = 0.f;
         const bool act = lane < nb;
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        uint32_t qo = (uint32_t)lane;
-        if (act) {
-            const uint32_t slot = (head + (uint32_t)lane) & (kQueue - 1);
-            q = s_q[warp][slot];  // (d, j)
-            qo = s_qo[warp][slot];
-        }
-        // the owning particle's data, at its index held by the owner lane
-        const uint32_t oidx = __shfl_sync(0xFFFFFFFFu, own_idx, (int)(qo & 31u));
         uint32_t owner = 32u + (uint32_t)lane;  // distinct dummy owners for idle lanes
         if (act) {
+            const uint32_t slot = (head + (uint32_t)lane) & (kQueue - 1);
+            const float4 q = w.q[slot];  // (d, j)
+            const uint32_t qo = w.qo[slot];
             owner = qo & 31u;
-            const float4 wi = __ldg(vel + oidx);
+            const float4 wi = w.vi[owner];
             const float4 vj = __ldg(vel + __float_as_uint(q.w));
             const float dx = q.x, dy = q.y, dz = q.z;
             const float d2 = dist2_rn(dx, dy, dz);
             const float inv_r = rsqrtf(d2);
             const float r = d2 * inv_r;
-            const float w = fmaxf(fmaf(-r, P.inv_rc, 1.0f), 0.0f);
-            const float wR = weight_R<SMODE>(w, P.s);
+            const float wgt = fmaxf(fmaf(-r, P.inv_rc, 1.0f), 0.0f);
+            const float wR = weight_R<SMODE>(wgt, P.s);
             // e_ij = -d / r; e . v_ij = -(d . (v_i - v_j)) / r
             const float ev = -((dx * (wi.x - vj.x) + dy * (wi.y - vj.y)) + dz * (wi.z - vj.z)) * inv_r;
             uint32_t A, B;
             pair_hash(__float_as_uint(wi.w), __float_as_uint(vj.w), key, A, B);
             const float xi = gauss_from_hash(A, B);
-            const float a = ONE_SPECIES ? P.a[0]
-                                        : a_tab[__float_as_int(__ldg(pos + oidx).w) * P.n_species + (int)(qo >> 5)];
-            const float F = fmaf(a, w, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
+            const float a = ONE_SPECIES ? P.a[0] : a_tab[__float_as_int(w.pi[owner].w) * P.n_species + (int)(qo >> 5)];
+            const float F = fmaf(a, wgt, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
             const float sc = -F * inv_r;
             fx = sc * dx;
             fy = sc * dy;
             fz = sc * dz;
-            // Newton's third law: the partner (a later row) gets -F once
+            // Newton's third law: the partner gets -F once
             if (N3) red_add_f4(facc + __float_as_uint(q.w), -fx, -fy, -fz);
         }
-        // per-owner sums in lane order; the lowest lane of each group adds
-        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, owner);
-        const bool leader = (grp & lt_mask) == 0u;
-        int gmax = __popc(grp);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) gmax = max(gmax, __shfl_xor_sync(0xFFFFFFFFu, gmax, o));
+        // Per-owner sums: the queue follows the list, whose entries come
+        // owner by owner, so a batch holds a few runs of equal owners.  A
+        // segmented inclusive scan (fixed order) leaves each run's sum on its
+        // last lane, which adds it to the owner's accumulator.
+        const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, owner, 1);
+        const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != owner);
+        const int start = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));  // first lane of the run
         float sx = fx, sy = fy, sz = fz;
-        uint32_t rest = grp & (grp - 1u);  // group members after the lowest, in lane order
-        for (int t = 1; t < gmax; ++t) {
-            const int src = rest ? __ffs(rest) - 1 : lane;
-            const float ax = __shfl_sync(0xFFFFFFFFu, fx, src);
-            const float ay = __shfl_sync(0xFFFFFFFFu, fy, src);
-            const float az = __shfl_sync(0xFFFFFFFFu, fz, src);
-            if (rest) {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float ax = __shfl_up_sync(0xFFFFFFFFu, sx, d);
+            const float ay = __shfl_up_sync(0xFFFFFFFFu, sy, d);
+            const float az = __shfl_up_sync(0xFFFFFFFFu, sz, d);
+            if (lane - start >= d) {
                 sx += ax;
                 sy += ay;
                 sz += az;
             }
-            rest &= rest - 1u;
         }
-        if (leader && owner < 32u) {
-            s_acc[warp][0][owner] += sx;
-            s_acc[warp][1][owner] += sy;
-            s_acc[warp][2][owner] += sz;
+        const bool tail_lane = owner < 32u && (lane == 31 || ((heads >> lane) & 2u) != 0u);
+        if (N3) {
+            // an owner can recur in a later run of the batch: atomics
+            if (tail_lane) {
+                atomicAdd(&w.acc[0][owner], sx);
+                atomicAdd(&w.acc[1][owner], sy);
+                atomicAdd(&w.acc[2][owner], sz);
+            }
+        } else {
+            // fixed order: the runs add in lane order
+            uint32_t tails = __ballot_sync(0xFFFFFFFFu, tail_lane);
+            while (tails) {
+                const int src = __ffs(tails) - 1;
+                if (lane == src) {
+                    w.acc[0][owner] += sx;
+                    w.acc[1][owner] += sy;
+                    w.acc[2][owner] += sz;
+                }
+                tails &= tails - 1u;
+                __syncwarp();
+            }
         }
         __syncwarp();
     };
 
     uint32_t head = 0u, tail = 0u;
-    // one candidate: test it, queue it if inside r_c, evaluate a full batch
-    auto candidate = [&](int k, uint32_t j, float4 pj) {
-        const float3 d = pair_delta<WRAP>(P, pj, pi);
+    // one candidate (entry e, partner position pj): test it, queue it if
+    // inside r_c, evaluate a full batch
+    auto candidate = [&](bool act, uint32_t e, float4 pj) {
+        const uint32_t own = e >> kOwnerShift;
+        const float3 d = pair_delta<WRAP>(P, pj, w.pi[own]);
         const float d2 = dist2_rn(d.x, d.y, d.z);
         // bitwise & keeps the test branch-free (no short-circuit evaluation)
-        const bool hit = (k < cnt) & (d2 < P.rc2) & (d2 > 0.0f);
+        const bool hit = act & (d2 < P.rc2) & (d2 > 0.0f);
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
         if (hit) {
             const uint32_t slot = (tail + (uint32_t)__popc(m & lt_mask)) & (kQueue - 1);
-            s_q[warp][slot] = make_float4(d.x, d.y, d.z, __uint_as_float(j));
-            s_qo[warp][slot] = (uint8_t)((uint32_t)lane | (ONE_SPECIES ? 0u : ((uint32_t)__float_as_int(pj.w) << 5)));
+            w.q[slot] = make_float4(d.x, d.y, d.z, __uint_as_float(e & kIndexMask));
+            w.qo[slot] = (uint8_t)(own | (ONE_SPECIES ? 0u : ((uint32_t)__float_as_int(pj.w) << 5)));
         }
         tail += (uint32_t)__popc(m);
         __syncwarp();
@@ -337,22 +368,22 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             head += 32u;
         }
     };
-    // 32-bit rows, entry k at k * 32.  Row entries are loaded four candidates
-    // ahead through a register rotation (the loop stays rolled: the batch
-    // evaluation inside it is large), and each candidate's position one ahead.
-    uint32_t q0 = cnt > 0 ? __ldg(row + lane) : self;
-    uint32_t q1 = cnt > 1 ? __ldg(row + 32 + lane) : self;
-    uint32_t q2 = cnt > 2 ? __ldg(row + 64 + lane) : self;
-    uint32_t q3 = cnt > 3 ? __ldg(row + 96 + lane) : self;
-    float4 pc = __ldg(pos + q0);
-    for (int k = 0; k < maxcnt; ++k) {
-        const uint32_t q4 = k + 4 < cnt ? __ldg(row + (size_t)(k + 4) * 32 + lane) : self;
-        const float4 pn = __ldg(pos + q1);
-        candidate(k, q0, pc);
-        q0 = q1;
-        q1 = q2;
-        q2 = q3;
-        q3 = q4;
+    // Entries are loaded four iterations ahead through a register rotation
+    // (the loop stays rolled: the batch evaluation inside it is large), and
+    // each candidate's position one ahead.  Past the end a lane reads entry 0
+    // (owner 0, particle 0), a valid address that the act flag discards.
+    auto entry = [&](uint32_t k) -> uint32_t { return k < nent ? __ldg(list + k) : 0u; };
+    const uint32_t l = (uint32_t)lane;
+    uint32_t e0 = entry(l), e1 = entry(32u + l), e2 = entry(64u + l), e3 = entry(96u + l);
+    float4 pc = __ldg(pos + (e0 & kIndexMask));
+    for (uint32_t base = 0; base < nent; base += 32u) {
+        const uint32_t e4 = entry(base + 128u + l);
+        const float4 pn = __ldg(pos + (e1 & kIndexMask));
+        candidate(base + l < nent, e0, pc);
+        e0 = e1;
+        e1 = e2;
+        e2 = e3;
+        e3 = e4;
         pc = pn;
     }
     while (tail != head) {
@@ -366,9 +397,7 @@ template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF, bool N3>
 __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, int out_fout)
 {
     constexpr int W = kForceThreads / 32;
-    __shared__ float s_acc[W][3][32];
-    __shared__ float4 s_q[W][kQueue];
-    __shared__ uint8_t s_qo[W][kQueue];
+    __shared__ WarpSmem s_w[W];
     __shared__ float a_tab[kMaxSpecies * kMaxSpecies];
     if (!ONE_SPECIES) {
         for (int k = threadIdx.x; k < P.n_species * P.n_species; k += blockDim.x) a_tab[k] = P.a[k];
@@ -379,38 +408,37 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     const uint32_t opar = ctl->oparity;
     const unsigned long long step0 = ctl->step;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * kForceThreads + threadIdx.x;
-    const bool valid = i < P.n;
+    WarpSmem &w = s_w[warp];
+    const uint32_t gid = blockIdx.x * W + (uint32_t)warp;
+    const uint2 desc = gid < (uint32_t)P.ngroups ? D.gdesc[gid] : make_uint2(0u, 0u);
+    const uint32_t owners = desc.y & 63u, nent = desc.y >> 6;
+    const int i = (int)desc.x + lane;
+    const bool valid = (uint32_t)lane < owners;
     const float4 *__restrict__ pos = D.pos[par];
     const float4 *__restrict__ vel = D.vel[par];
     const float4 pi = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const float4 vi = valid ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    s_acc[warp][0][lane] = 0.f;
-    s_acc[warp][1][lane] = 0.f;
-    s_acc[warp][2][lane] = 0.f;
-    const int cnt = valid ? (int)D.nnb[i] : 0;
-    int maxcnt = cnt;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxcnt = max(maxcnt, __shfl_xor_sync(0xFFFFFFFFu, maxcnt, o));
-    const uint32_t *__restrict__ row = D.nbr + (size_t)(i >> 5) * P.cap * 32;  // tile of the warp
-    const uint32_t self = valid ? (uint32_t)i : 0u;
+    w.pi[lane] = pi;
+    w.vi[lane] = vi;
+    w.acc[0][lane] = 0.f;
+    w.acc[1][lane] = 0.f;
+    w.acc[2][lane] = 0.f;
     // the warp may skip the minimum image when all its particles are far from the faces
     const bool interior = !valid || (pi.x >= P.wrap_margin && pi.x <= P.L[0] - P.wrap_margin &&
                                      pi.y >= P.wrap_margin && pi.y <= P.L[1] - P.wrap_margin &&
                                      pi.z >= P.wrap_margin && pi.z <= P.L[2] - P.wrap_margin);
     const bool all_interior = __all_sync(0xFFFFFFFFu, interior) && P.wrap_margin > 0.0f;
     __syncwarp();
+    const uint32_t *__restrict__ list = D.nbr + (size_t)gid * P.gcap;
     if (all_interior)
-        warp_pairs<ONE_SPECIES, SMODE, false, N3>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
-                                                  s_acc, a_tab, warp, D.facc);
+        warp_pairs<ONE_SPECIES, SMODE, false, N3>(P, pos, vel, list, nent, lane, w, a_tab, D.facc);
     else
-        warp_pairs<ONE_SPECIES, SMODE, true, N3>(P, pos, vel, row, cnt, maxcnt, self, self, pi, lane, s_q, s_qo,
-                                                 s_acc, a_tab, warp, D.facc);
-    float fx = s_acc[warp][0][lane], fy = s_acc[warp][1][lane], fz = s_acc[warp][2][lane];
+        warp_pairs<ONE_SPECIES, SMODE, true, N3>(P, pos, vel, list, nent, lane, w, a_tab, D.facc);
+    float fx = w.acc[0][lane], fy = w.acc[1][lane], fz = w.acc[2][lane];
 
     if (N3) {
-        // this row's share of particle i's force; the settle kernel adds the
-        // shares other rows pushed into facc and completes the mode
+        // this group's share of particle i's force; the settle kernel adds
+        // the shares other groups pushed into facc and completes the mode
         if (valid) {
             add_bonds_body(P, D, i, pi, pos, opar, fx, fy, fz);
             D.fown[i] = make_float4(fx, fy, fz, 0.0f);
@@ -437,11 +465,11 @@ __global__ void __launch_bounds__(kThreads) k_settle(SimParams P, Ptrs D, int ou
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         const float4 a = D.fown[i];
         const float4 b = D.facc[i];
-        D.facc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 pi = D.pos[par][i];
         const float4 vi = D.vel[par][i];
         moved |= integrate_particle<MODE, LHALF>(P, D, ctl, i, pi, vi, a.x + b.x, a.y + b.y, a.z + b.z, par, opar,
                                                  step0, out_fout);
+        D.facc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (MODE != kForceEval) finish_block(ctl, moved);
 }
@@ -582,7 +610,7 @@ constexpr int kMaxDynSmem = 160 * 1024;  // largest staging buffer the brick bui
 template <bool ONE, int MODE, bool LH, bool N3>
 cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream_t s)
 {
-    const int g = (P.n + kForceThreads - 1) / kForceThreads;
+    const int g = (P.ngroups + kForceThreads / 32 - 1) / (kForceThreads / 32);
     switch (P.s_mode) {
     case 1: k_force<ONE, 1, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
     case 2: k_force<ONE, 2, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;

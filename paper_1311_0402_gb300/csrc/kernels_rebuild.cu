@@ -231,58 +231,118 @@ __global__ void k_commit(Ptrs D)
     c->max_nnb = 0u;
 }
 
+// ---------------------------------------------------------------------------
+// Neighbour build into packed group lists.  A warp builds one group: lane l
+// owns particle first + l and walks its own candidate sequence (the
+// particles of its surrounding cells, cell by cell, each cell in index
+// order); all lanes take one candidate per iteration in lockstep, and the
+// hits of an iteration are compacted with a ballot and appended to the
+// group's list in lane order.  The list content and order depend only on the
+// positions: deterministic, with no atomics.  In Newton-3 mode a particle
+// keeps only partners j > i, and a cell's walk starts past i.
+
+// Append the hits of one lockstep iteration to a group list; returns the
+// group's new running total (entries past gcap are counted, not written).
+__device__ __forceinline__ uint32_t append_hits(bool hit, uint32_t lane, uint32_t j, uint32_t total,
+                                                uint32_t *list, uint32_t gcap)
+{
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+    if (hit) {
+        const uint32_t k = total + (uint32_t)__popc(m & ((1u << lane) - 1u));
+        if (k < gcap) list[k] = (lane << kOwnerShift) | j;
+    }
+    return total + (uint32_t)__popc(m);
+}
+
+// Group descriptor and overflow flag, written by lane 0.
+__device__ __forceinline__ void write_group(const Ptrs &D, const SimParams &P, uint32_t g, uint32_t first,
+                                            uint32_t owners, uint32_t total)
+{
+    const uint32_t ne = total < (uint32_t)P.gcap ? total : (uint32_t)P.gcap;
+    D.gdesc[g] = make_uint2(first, owners | (ne << 6));
+    if (total > (uint32_t)P.gcap) atomicOr(&D.ctl->err, kErrNbrOverflow);
+}
+
+// Builder for grids with fewer than three cells along some axis (no
+// bricks): groups are the 32-aligned tiles, candidates come from the
+// deduplicated cell stencil in global memory.
 __global__ void k_nbuild(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
     const uint32_t par = D.ctl->parity;
-    const float4 *pos = D.pos[par];
+    const float4 *__restrict__ pos = D.pos[par];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nwarps = gridDim.x * blockDim.x / 32u;
     uint32_t local_max = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        float4 pi = pos[i];
-        uint32_t c = cell_rank_of(P, D.rank_of_cell, pi, nullptr);
-        const uint32_t *st = D.stencil + (size_t)c * kStencil;
-        uint32_t *row = D.nbr + (size_t)(i >> 5) * P.cap * 32 + (i & 31);
-        uint32_t cnt = 0;
-        for (int s = 0; s < kStencil; ++s) {
-            uint32_t cc = st[s];
-            if (cc == kNone) break;
-            uint32_t b = D.cell_start[cc], e = D.cell_start[cc + 1];
-            for (uint32_t j = b; j < e; ++j) {
-                if (P.newton3 ? j <= (uint32_t)i : j == (uint32_t)i) continue;
-                float4 pj = pos[j];
-                float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-                float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-                float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-                if (dist2_rn(dx, dy, dz) < P.rlist2) {
-                    if (cnt < (uint32_t)P.cap) row[(size_t)cnt * 32] = j;
-                    ++cnt;
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) / 32u; g < (uint32_t)P.ngroups; g += nwarps) {
+        const uint32_t i = g * kGroup + lane;
+        const bool valid = i < (uint32_t)P.n;
+        const float4 pi = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const uint32_t *st = D.stencil + (size_t)(valid ? cell_rank_of(P, D.rank_of_cell, pi, nullptr) : 0u) * kStencil;
+        uint32_t s = valid ? 0u : (uint32_t)kStencil, b = 0, n = 0, e = 0;
+        auto next_cell = [&]() {
+            while (e >= n && s < (uint32_t)kStencil) {
+                const uint32_t cc = st[s++];
+                if (cc == kNone) {
+                    s = kStencil;
+                    break;
                 }
+                b = D.cell_start[cc];
+                n = D.cell_start[cc + 1] - b;
+                e = (P.newton3 && i >= b) ? i + 1u - b : 0u;
             }
+        };
+        next_cell();
+        uint32_t *list = D.nbr + (size_t)g * P.gcap;
+        uint32_t total = 0;
+        for (;;) {
+            const bool act = e < n;
+            if (!__any_sync(0xFFFFFFFFu, act)) break;
+            bool hit = false;
+            uint32_t j = 0;
+            if (act) {
+                j = b + e;
+                const float4 pj = pos[j];
+                const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+                const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+                const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+                hit = (dist2_rn(dx, dy, dz) < P.rlist2) & (P.newton3 || j != i);
+                ++e;
+                if (e >= n) next_cell();
+            }
+            total = append_hits(hit, lane, j, total, list, (uint32_t)P.gcap);
         }
-        if (cnt > (uint32_t)P.cap) atomicOr(&D.ctl->err, kErrNbrOverflow);
-        D.nnb[i] = cnt < (uint32_t)P.cap ? cnt : (uint32_t)P.cap;
-        local_max = cnt > local_max ? cnt : local_max;
+        if (lane == 0) {
+            const uint32_t owners = (uint32_t)P.n - g * kGroup < 32u ? (uint32_t)P.n - g * kGroup : 32u;
+            write_group(D, P, g, g * kGroup, owners, total);
+        }
+        local_max = total > local_max ? total : local_max;
     }
-    // warp max, then one atomic per warp
-    for (int o = 16; o > 0; o >>= 1) {
-        uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, local_max, o);
-        local_max = y > local_max ? y : local_max;
-    }
-    if ((threadIdx.x & 31) == 0) atomicMax(&D.ctl->max_nnb, local_max);
+    if (lane == 0 && local_max) atomicMax(&D.ctl->max_nnb, local_max);
 }
 
-// Neighbour build, one CTA per brick (see brick.cuh).  In Newton-3 mode the
-// rows keep only partners j > i (half rows), and stencil cells whose
-// particles all precede i are skipped outright.  The CTA stages the
-// positions of the brick's halo in shared memory with bulk (TMA) copies; each
-// thread owns one particle of the brick and tests the particles of its 27
-// surrounding cells, read from shared memory, with the FP32 predicate,
-// appending hits to its own row in the fixed stencil order (dz, dy, dx =
-// -1..1, each cell in index order): deterministic rows with no votes or
-// atomics.  Stencil cells whose nearest point lies beyond r_list are skipped.
-// A brick whose halo exceeds the staging buffer reads positions from global
-// memory.
+// Brick builder: one CTA per brick (see brick.cuh).  The CTA stages the
+// positions of the brick's halo in shared memory with bulk (TMA) copies;
+// its warps take the brick's particles in groups of 32 and build each
+// group cell by cell.  For a cell C the warp lays out one candidate
+// sequence: C's own particles (index order), then the particles of the
+// stencil cells it needs -- in Newton-3 mode those of higher rank than C,
+// otherwise all 26 -- and copies it, in chunks, to a per-warp buffer
+// (position, index).  The candidates j > i of an owner i at place p of C are
+// then exactly the suffix from p + 1 on, because cells are index ranges in
+// rank order; full lists take the whole sequence minus i.  For each owner of
+// the group in C, all 32 lanes test 32 consecutive candidates per
+// iteration, the owner's position broadcast from shared memory, and append
+// the hits with a ballot.  No lane diverges and the list order is fixed by
+// the positions.  The groups of brick b get the ids lo/32 + ord(b) onwards,
+// where ord is the brick's position in rank order: unique ids with no count
+// pass; the ids a brick leaves unused (at most one or two) get empty
+// descriptors.  A brick whose halo exceeds the staging buffer reads
+// positions from global memory.
 constexpr int kBuildThreads = 256;
+constexpr int kBuildWarps = kBuildThreads / 32;
+constexpr int kSlots = 4;               // candidates per lane and chunk, held in registers
+constexpr int kChunk = 32 * kSlots;     // chunk of the candidate sequence
 
 template <bool WRAP>
 __device__ __forceinline__ bool within_list(const SimParams &P, float4 pj, float4 pi)
@@ -300,124 +360,208 @@ __device__ __forceinline__ bool within_list(const SimParams &P, float4 pj, float
     return dist2_rn(dx, dy, dz) < P.rlist2;
 }
 
-// Squared distance from a particle at fractional position f (in units of the
-// cell side, per axis) in its cell to the neighbour cell at offset o, along
-// the axis: 0 for the same slab, f for the slab below, 1 - f for the slab
-// above; times the squared side.  A cell whose nearest point is farther than
-// r_list (with a margin far above FP32 rounding of positions and cell
-// indices) holds no particle the predicate can admit and is skipped.
-__device__ __forceinline__ float slab_gap(float f, int o, float side)
-{
-    const float g = o < 0 ? f : (o > 0 ? 1.0f - f : 0.0f);
-    const float d = fmaxf(g * side - 1e-4f, 0.0f);
-    return d * d;
-}
+// Per-warp table of one slot of the candidate sequence: head[l] is the
+// sequence entry (cell) whose first candidate falls on lane l.
+struct CellSeq {
+    uint8_t head[32];
+};
 
-// Row of one particle: the particles of its 27 surrounding cells (stencil
-// order dz, dy, dx = -1..1, each cell in index order) that pass the FP32
-// predicate, as 32-bit global indices in the particle's row of its 32-wide
-// tile (entry k at k * 32).  Candidate positions come from the staged halo
-// (STAGED) or from global memory.
+// The owners [p_lo, p_hi) (places in cell slot t) of a group whose first
+// particle is `first`: their pairs with the candidate sequence, appended to
+// the group list; returns the new running total.  A chunk of kChunk
+// candidates is held in registers, lane l holding entries c0 + 32 s + l;
+// every owner of the cell tests against the same registers.
 template <bool WRAP, bool STAGED, bool HALF>
-__device__ __forceinline__ uint32_t build_row(const SimParams &P, const float4 *pos, const float4 *s_pos,
-                                              const uint32_t *s_off, const uint32_t *s_gstart,
-                                              const uint32_t *s_cnt, int hx, int hy, int hz, const float *frac,
-                                              uint32_t i, float4 pi, uint32_t *row, uint32_t cap)
+__device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 *__restrict__ pos,
+                                               const float4 *s_pos, const uint32_t *s_off, const uint32_t *s_gstart,
+                                               const uint32_t *s_cnt, CellSeq &w, int t, uint32_t p_lo, uint32_t p_hi,
+                                               uint32_t first, uint32_t lane, uint32_t *list, uint32_t gcap,
+                                               uint32_t total)
 {
-    const float side[3] = {P.L[0] / (float)P.nc[0], P.L[1] / (float)P.nc[1], P.L[2] / (float)P.nc[2]};
-    uint32_t cnt = 0;
-    for (int oz = -1; oz <= 1; ++oz) {
-        const float gz = slab_gap(frac[2], oz, side[2]);
-        for (int oy = -1; oy <= 1; ++oy) {
-            const float gyz = gz + slab_gap(frac[1], oy, side[1]);
-            for (int ox = -1; ox <= 1; ++ox) {
-                if (gyz + slab_gap(frac[0], ox, side[0]) >= P.rlist2) continue;
-                const int t = brick_halo_slot(hx + ox, hy + oy, hz + oz);
-                const uint32_t o = s_off[t], g = s_gstart[t], n = s_cnt[t];
-                if (HALF && g + n <= i + 1u) continue;  // every particle of the cell precedes i
-                for (uint32_t e = 0; e < n; ++e) {
-                    const uint32_t j = g + e;
-                    const float4 pj = STAGED ? s_pos[o + e] : pos[j];
-                    const bool hit = within_list<WRAP>(P, pj, pi) & (HALF ? (j > i) : (j != i));
-                    if (hit & (cnt < cap)) row[(size_t)cnt * 32] = j;
-                    cnt += hit ? 1u : 0u;
+    const uint32_t g_own = s_gstart[t], n_own = s_cnt[t];
+    // lanes 0..26: stencil cell (dz, dy, dx) = (l / 9, l / 3 % 3, l % 3) - 1;
+    // lane 13 is the cell itself
+    uint32_t n_use = 0;
+    int ts = t;
+    if (lane < (uint32_t)kStencil) {
+        ts = t + ((int)(lane / 9u) - 1) * (kHalo * kHalo) + ((int)(lane / 3u % 3u) - 1) * kHalo + ((int)(lane % 3u) - 1);
+        const uint32_t n = s_cnt[ts];
+        const bool use = lane != 13u && (!HALF || s_gstart[ts] > g_own);
+        n_use = use ? n : 0u;
+    }
+    uint32_t incl = n_use;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    const uint32_t total_seq = n_own + __shfl_sync(0xFFFFFFFFu, incl, 31);
+    // this lane's sequence entry (lanes 0..26): own cell first (lane 13),
+    // then the used stencil cells in lane order
+    const uint32_t my_start = lane == 13u ? 0u : n_own + incl - n_use;
+    const uint32_t my_n = lane == 13u ? n_own : n_use;
+    const uint32_t my_g = lane < (uint32_t)kStencil ? s_gstart[ts] : 0u;
+    const uint32_t my_o = lane < (uint32_t)kStencil ? s_off[ts] : 0u;
+    for (uint32_t c0 = 0; c0 < total_seq; c0 += (uint32_t)kChunk) {
+        const uint32_t c1 = min(total_seq, c0 + (uint32_t)kChunk);
+        float4 cand[kSlots];
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const uint32_t kb = c0 + 32u * sl;
+            cand[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kb < c1) {
+                // the cell of candidate kb + lane: the last cell starting at or
+                // below it in this slot, else the cell covering kb
+                const bool covers = my_n > 0u && my_start <= kb && kb < my_start + my_n;
+                const bool starts = my_n > 0u && my_start > kb && my_start < kb + 32u;
+                if (covers) w.head[0] = (uint8_t)lane;
+                if (starts) w.head[my_start - kb] = (uint8_t)lane;
+                const uint32_t hmask = __reduce_or_sync(0xFFFFFFFFu, starts ? 1u << (my_start - kb) : 0u) | 1u;
+                __syncwarp();
+                const int h = 31 - __clz(hmask & (0xFFFFFFFFu >> (31u - lane)));
+                const int c = w.head[h];
+                __syncwarp();
+                const uint32_t cs = __shfl_sync(0xFFFFFFFFu, my_start, c);
+                const uint32_t cg = __shfl_sync(0xFFFFFFFFu, my_g, c);
+                const uint32_t co = __shfl_sync(0xFFFFFFFFu, my_o, c);
+                const uint32_t k = kb + lane;
+                if (k < c1) {
+                    const uint32_t e = k - cs;
+                    const uint32_t j = cg + e;
+                    float4 pj = STAGED ? s_pos[co + e] : pos[j];
+                    pj.w = __uint_as_float(j);
+                    cand[sl] = pj;
                 }
             }
         }
+        // owners two at a time: all ballots first (independent work), then
+        // each owner's hits are appended in turn, so an owner's entries stay
+        // contiguous in the list
+        for (uint32_t p = p_lo; p < p_hi; p += 2u) {
+            const bool two = p + 1u < p_hi;
+            const uint32_t ia = g_own + p, ib = ia + (two ? 1u : 0u);
+            const float4 pa = STAGED ? s_pos[s_off[t] + p] : pos[ia];
+            const float4 pb = STAGED ? s_pos[s_off[t] + (ib - g_own)] : pos[ib];
+            const uint32_t k0a = HALF ? max(p + 1u, c0) : c0;
+            const uint32_t k0b = HALF ? max(p + 2u, c0) : c0;
+            uint32_t ma[kSlots], mb[kSlots];
+#pragma unroll
+            for (int sl = 0; sl < kSlots; ++sl) {
+                const uint32_t kb = c0 + 32u * sl;
+                ma[sl] = 0u;
+                mb[sl] = 0u;
+                if (kb < c1 && kb + 32u > k0a) {
+                    const uint32_t k = kb + lane;
+                    const uint32_t j = __float_as_uint(cand[sl].w);
+                    const bool in = k < c1;
+                    ma[sl] = __ballot_sync(0xFFFFFFFFu, in & (k >= k0a) & within_list<WRAP>(P, cand[sl], pa) &
+                                                            (HALF || j != ia));
+                    mb[sl] = __ballot_sync(0xFFFFFFFFu, two & in & (k >= k0b) & within_list<WRAP>(P, cand[sl], pb) &
+                                                            (HALF || j != ib));
+                }
+            }
+            const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+            for (int sl = 0; sl < kSlots; ++sl) {
+                if ((ma[sl] >> lane) & 1u) {
+                    const uint32_t q = total + (uint32_t)__popc(ma[sl] & lt);
+                    if (q < gcap) list[q] = ((ia - first) << kOwnerShift) | __float_as_uint(cand[sl].w);
+                }
+                total += (uint32_t)__popc(ma[sl]);
+            }
+#pragma unroll
+            for (int sl = 0; sl < kSlots; ++sl) {
+                if ((mb[sl] >> lane) & 1u) {
+                    const uint32_t q = total + (uint32_t)__popc(mb[sl] & lt);
+                    if (q < gcap) list[q] = ((ib - first) << kOwnerShift) | __float_as_uint(cand[sl].w);
+                }
+                total += (uint32_t)__popc(mb[sl]);
+            }
+        }
     }
-    return cnt;
+    return total;
 }
 
-__global__ void __launch_bounds__(kBuildThreads) k_nbuild_brick(SimParams P, Ptrs D)
+__global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
     extern __shared__ float4 s_pos[];  // [P.brick_cap] staged halo positions
     __shared__ uint32_t s_off[kHaloCells + 1];
     __shared__ uint32_t s_gstart[kHaloCells];
     __shared__ uint32_t s_cnt[kHaloCells];
-    __shared__ uint32_t s_wsum[kBuildThreads / 32];
+    __shared__ uint32_t s_wsum[kBuildWarps];
     __shared__ __align__(8) uint64_t s_bar;
+    __shared__ CellSeq s_seq[kBuildWarps];
     const uint32_t par = D.ctl->parity;
     const float4 *pos = D.pos[par];
     const int b = blockIdx.x;
     const BrickRange br = brick_halo(P, D, b, s_off, s_gstart, s_cnt, s_wsum);
+    const uint32_t ord = D.brick_ord[b];
+    const uint32_t gbase = br.lo / kGroup + ord, gnext = br.hi / kGroup + ord + 1u;
+    const uint32_t nloc = br.hi - br.lo, ngrp = (nloc + kGroup - 1) / kGroup;
     const bool local = s_off[kHaloCells] <= (uint32_t)P.brick_cap;  // halo fits the staging buffer
     bool staged = true;
     if (local) staged = brick_stage_bulk(D, &s_bar, s_pos, pos, nullptr, nullptr, s_off, s_gstart, s_cnt);
-    if (!staged) {  // the error word is set; leave no rows behind for the force kernel
-        for (uint32_t i = br.lo + threadIdx.x; i < br.hi; i += blockDim.x) D.nnb[i] = 0u;
+    if (!staged) {  // the error word is set; leave no lists behind for the force kernel
+        for (uint32_t g = gbase + threadIdx.x; g < gnext; g += blockDim.x) D.gdesc[g] = make_uint2(0u, 0u);
         return;
     }
     const int bx = b % P.nb[0], by = (b / P.nb[0]) % P.nb[1], bz = b / (P.nb[0] * P.nb[1]);
-    const uint32_t cap = (uint32_t)P.cap;
+    const uint32_t gcap = (uint32_t)P.gcap;
     const bool grid5 = P.nc[0] >= 5 && P.nc[1] >= 5 && P.nc[2] >= 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    CellSeq &w = s_seq[threadIdx.x / 32u];
     uint32_t local_max = 0;
-    const uint32_t nloc = br.hi - br.lo;
-    for (uint32_t p0 = 0; p0 < nloc; p0 += blockDim.x) {
-        const uint32_t p = p0 + threadIdx.x;
-        const bool valid = p < nloc;
-        const uint32_t i = br.lo + p;
-        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-        int cx = 1, cy = 1, cz = 1;
-        float fx_ = 0.f, fy_ = 0.f, fz_ = 0.f;
-        if (valid) {
-            pi = pos[i];
-            cx = cell_axis(pi.x, P.cells_per_len[0], P.nc[0], &fx_);
-            cy = cell_axis(pi.y, P.cells_per_len[1], P.nc[1], &fy_);
-            cz = cell_axis(pi.z, P.cells_per_len[2], P.nc[2], &fz_);
+    for (uint32_t q = threadIdx.x / 32u; q < ngrp; q += kBuildWarps) {
+        const uint32_t first = br.lo + q * kGroup;
+        const uint32_t owners = nloc - q * kGroup < (uint32_t)kGroup ? nloc - q * kGroup : (uint32_t)kGroup;
+        // halo slot of each lane's cell (the own cells of the brick are at 1..kBrick per axis)
+        int t_lane = -1, inner_lane = 1;
+        if (lane < owners) {
+            const float4 pi = pos[first + lane];
+            float f;
+            const int cx = cell_axis(pi.x, P.cells_per_len[0], P.nc[0], &f);
+            const int cy = cell_axis(pi.y, P.cells_per_len[1], P.nc[1], &f);
+            const int cz = cell_axis(pi.z, P.cells_per_len[2], P.nc[2], &f);
+            t_lane = brick_halo_slot(cx - bx * kBrick + 1, cy - by * kBrick + 1, cz - bz * kBrick + 1);
+            // a cell one layer or more inside a grid of >= 5 cells per axis
+            // never sees a periodic image in its stencil
+            inner_lane = grid5 && cx >= 1 && cx <= P.nc[0] - 2 && cy >= 1 && cy <= P.nc[1] - 2 && cz >= 1 &&
+                         cz <= P.nc[2] - 2;
         }
-        const int hx = cx - bx * kBrick + 1, hy = cy - by * kBrick + 1, hz = cz - bz * kBrick + 1;  // 1..kBrick
-        // a cell one layer or more inside a grid of >= 5 cells per axis never
-        // sees a periodic image in its stencil: the whole warp can skip the
-        // minimum image when all its particles sit in such cells
-        const bool inner = grid5 && cx >= 1 && cx <= P.nc[0] - 2 && cy >= 1 && cy <= P.nc[1] - 2 && cz >= 1 &&
-                           cz <= P.nc[2] - 2;
-        const bool warp_inner = __all_sync(0xFFFFFFFFu, inner || !valid);
-        if (!valid) continue;
-        uint32_t *row = D.nbr + (size_t)(i >> 5) * cap * 32 + (i & 31u);
-        const float frac[3] = {fx_, fy_, fz_};
-        uint32_t cnt;
-        if (P.newton3) {
-            if (local)
-                cnt = warp_inner
-                          ? build_row<false, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap)
-                          : build_row<true, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
-            else
-                cnt = build_row<true, false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
-        } else {
-            if (local)
-                cnt = warp_inner
-                          ? build_row<false, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap)
-                          : build_row<true, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
-            else
-                cnt = build_row<true, false, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, hx, hy, hz, frac, i, pi, row, cap);
+        uint32_t *list = D.nbr + (size_t)(gbase + q) * gcap;
+        uint32_t total = 0;
+        // the group's particles are sorted by cell: take the cells in turn
+        for (uint32_t l0 = 0; l0 < owners;) {
+            const int t = __shfl_sync(0xFFFFFFFFu, t_lane, (int)l0);
+            const uint32_t same = __ballot_sync(0xFFFFFFFFu, t_lane == t);
+            const uint32_t run = (uint32_t)__popc(same);  // lanes of this cell (consecutive)
+            const bool inner = __shfl_sync(0xFFFFFFFFu, inner_lane, (int)l0) != 0;
+            const uint32_t p_lo = first + l0 - s_gstart[t];
+            const uint32_t p_hi = p_lo + run;
+            if (P.newton3) {
+                if (!local)
+                    total = build_cell<true, false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                else if (inner)
+                    total = build_cell<false, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                else
+                    total = build_cell<true, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+            } else {
+                if (!local)
+                    total = build_cell<true, false, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                else if (inner)
+                    total = build_cell<false, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                else
+                    total = build_cell<true, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+            }
+            l0 += run;
         }
-        if (cnt > cap) atomicOr(&D.ctl->err, kErrNbrOverflow);
-        D.nnb[i] = min(cnt, cap);
-        local_max = max(local_max, cnt);
+        if (lane == 0) write_group(D, P, gbase + q, first, owners, total);
+        local_max = total > local_max ? total : local_max;
     }
-    for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xFFFFFFFFu, local_max, o));
-    if ((threadIdx.x & 31) == 0 && local_max) atomicMax(&D.ctl->max_nnb, local_max);
+    // ids of this brick's range that no group took
+    for (uint32_t g = gbase + ngrp + threadIdx.x; g < gnext; g += blockDim.x) D.gdesc[g] = make_uint2(0u, 0u);
+    if (lane == 0 && local_max) atomicMax(&D.ctl->max_nnb, local_max);
 }
 
 }  // namespace

@@ -38,7 +38,8 @@ def test_dense_clump_grows_capacity():
     v = rng.standard_normal(x.shape)
     g, o = make_pair(CFG)
     g.set_state(x, v)
-    assert g.info()["nbr_capacity"] > 400
+    # the automatic capacity for the mean density is 64; the clump needs more
+    assert g.info()["nbr_capacity"] > 128
     x32, v32, _ = g.state()
     assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, CFG["box"], 1.3))
     fo, _ = o.forces(x32, v32)
