@@ -162,9 +162,11 @@ typedef struct {
     double total_ms;        /* first to last event */
     double integrate_ms;    /* the opening velocity-Verlet phase 1 of the call */
     double rebuild_ms;      /* binning / scan / reorder / neighbour-list chain */
-    double force_ms;        /* fused pair force (+ bonds, body force, and the
-                               integration into the next step, which runs in
-                               the force kernel's epilogue) */
+    double force_ms;        /* the force phase: pair force, bonds, body force
+                               and the integration into the next step (in
+                               Newton-3 mode the pair kernel, then the settle
+                               kernel that completes the sums and integrates) */
+    double pair_ms;         /* the pair kernel alone (part of force_ms) */
     int64_t steps;
     int64_t force_launches;
     int64_t kernel_launches;

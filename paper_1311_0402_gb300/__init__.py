@@ -69,6 +69,7 @@ class dpd_step_times(ctypes.Structure):
         ("integrate_ms", ctypes.c_double),
         ("rebuild_ms", ctypes.c_double),
         ("force_ms", ctypes.c_double),
+        ("pair_ms", ctypes.c_double),
         ("steps", ctypes.c_int64),
         ("force_launches", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),

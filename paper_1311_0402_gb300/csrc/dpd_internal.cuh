@@ -114,7 +114,7 @@ struct Ptrs {
     uint32_t *tmp_idx;             // [n] particle index in scatter order
     unsigned long long *skey;      // [n] in-cell sort key in scatter order
     uint32_t *perm;                // [n] new position -> old position
-    uint32_t *idx_of_pid;          // [n] caller index -> current position
+    uint32_t *idx_of_pid;          // [n] caller index -> current position (maintained while bonds are set)
     // neighbours
     uint32_t *nbr;                 // packed group lists, [ngroups][gcap]
     uint2 *gdesc;                  // [ngroups] (first particle, owners | entries << 6)
@@ -136,6 +136,8 @@ cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s);
 // velocity-Verlet phase 1 from the full-step velocity, in place
 cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s);
 cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, int n_scan_blocks);
+// idx_of_pid for the live order (kept up to date by rebuilds only while bonds are set)
+cudaError_t launch_index(const SimParams &P, const Ptrs &D, cudaStream_t s);
 // Pair force.  kForceEval: the force of the live state into D.fout (out_fout)
 // or force[parity], nothing else changes.  kForceStep: force at the live
 // state, then phase 2 of this step and phase 1 of the next into the other
@@ -144,7 +146,11 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
 enum ForceMode { kForceEval = 0, kForceStep = 1, kForceFinish = 2 };
 // In Newton-3 mode the pair kernel only accumulates (fown, facc) and a
 // settle kernel completes the same mode afterwards; launch_force runs both.
-cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s);
+// after_pair (optional) is recorded with ev_flags right after the pair kernel.
+cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s,
+                         cudaEvent_t after_pair = nullptr, unsigned int ev_flags = 0);
+// observables: nblocks per-block partials in D.red, then their fixed-order
+// sum in D.red[nblocks * 8 .. + 8)
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s);
 cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int vel_axis, int nbins,
                            int nblocks, cudaStream_t s);
@@ -155,6 +161,6 @@ int scan_blocks_for(int ncell);
 cudaError_t init_kernel_attributes();
 // largest brick_cap the builder's shared-memory limit allows
 int max_brick_cap();
-int observe_blocks_for(int n);
+int observe_blocks_for(int ngroups);
 
 }  // namespace dpd

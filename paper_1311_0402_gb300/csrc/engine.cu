@@ -231,27 +231,32 @@ constexpr int kRebuildKernels = 9;  // bin, 3 scan, scatter, rank, gather, commi
 
 // Timing event on the stream; inside a graph capture it becomes an event
 // record node whose timestamp stays readable after the graph runs.
-cudaError_t rec(dpd_sim *h, cudaEvent_t e)
+// event record flags: external during stream capture (so the graph keeps
+// the records as timing nodes), plain otherwise
+unsigned int rec_flags(dpd_sim *h)
 {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    cudaError_t err = cudaStreamIsCapturing(h->stream, &cs);
-    if (err != cudaSuccess) return err;
-    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
-    return cudaEventRecord(e, h->stream);
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) return 0u;
+    return cs == cudaStreamCaptureStatusActive ? (unsigned int)cudaEventRecordExternal : 0u;
 }
 
+cudaError_t rec(dpd_sim *h, cudaEvent_t e) { return cudaEventRecordWithFlags(e, h->stream, rec_flags(h)); }
+
 // The kernel sequence of enqueue_steps with timing events between the
-// groups: ev[0] | phase 1 | ev[1] | rebuild | ev[2] | force (+ integrate) | ev[3] | rebuild | ev[4] ...
+// groups: ev[0] | phase 1 | ev[1] | rebuild | ev[2] | pair kernel | ev[3] |
+// settle + advance | ev[4] | rebuild | ev[5] ...  (3 events per step)
 cudaError_t enqueue_steps_timed(dpd_sim *h, int64_t k)
 {
     cudaError_t e = rec(h, h->tev[0]);
     if (e == cudaSuccess) e = launch_phase1(h->P, h->D, h->stream);
     if (e == cudaSuccess) e = rec(h, h->tev[1]);
+    const unsigned int fl = rec_flags(h);
     for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
         e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
-        if (e == cudaSuccess) e = rec(h, h->tev[2 * s + 2]);
-        if (e == cudaSuccess) e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream);
-        if (e == cudaSuccess) e = rec(h, h->tev[2 * s + 3]);
+        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 2]);
+        if (e == cudaSuccess)
+            e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream, h->tev[3 * s + 3], fl);
+        if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 4]);
     }
     return e;
 }
@@ -348,7 +353,7 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     h->P.ngroups = group_count(h, n);
     A((void **)&D.gdesc, sizeof(uint2) * (size_t)h->P.ngroups);
     A((void **)&D.nbr, (size_t)h->P.ngroups * kGroup * (size_t)cap * sizeof(uint32_t));
-    h->red_doubles = std::max<size_t>((size_t)observe_blocks_for((int)n) * 8, 4096);
+    h->red_doubles = std::max<size_t>((size_t)observe_blocks_for(h->P.ngroups) * 8 + 8, 4096);
     A((void **)&D.red, h->red_doubles * sizeof(double));
     A((void **)&D.bond_partner, sizeof(uint32_t) * (size_t)n * kMaxBonds);
     if (st) return st;
@@ -687,6 +692,7 @@ dpd_status dpd_set_bonds(dpd_sim *h, int64_t nb, const uint32_t *pairs, double k
     h->P.r0_bond = (float)r0;
     h->bonds_set = nb > 0;
     drop_graphs(h);
+    CUDA_TRY(h, launch_index(h->P, h->D, h->stream));
     CUDA_TRY(h, launch_force(h->P, h->D, kForceEval, false, h->stream));
     DevCtl c;
     return check_err(h, c);
@@ -830,7 +836,7 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
     dpd_status st = guard(h, true);
     if (st) return st;
     if (nsteps < 1 || nsteps > 100000) return fail(h, DPD_ERR_ARG, "nsteps must be in 1..100000");
-    const size_t nev = (size_t)(2 * nsteps + 2);
+    const size_t nev = (size_t)(3 * nsteps + 2);
     while (h->tev.size() < nev) {
         cudaEvent_t e;
         CUDA_TRY(h, cudaEventCreate(&e));
@@ -881,10 +887,11 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
         };
         out->integrate_ms = el(0, 1);
         for (int64_t s = 0; s < nsteps; ++s) {
-            out->rebuild_ms += el(s == 0 ? 1 : 2 * s + 1, 2 * s + 2);
-            out->force_ms += el(2 * s + 2, 2 * s + 3);
+            out->rebuild_ms += el(s == 0 ? 1 : 3 * s + 1, 3 * s + 2);
+            out->pair_ms += el(3 * s + 2, 3 * s + 3);
+            out->force_ms += el(3 * s + 2, 3 * s + 4);
         }
-        out->total_ms = el(0, 2 * nsteps + 1);
+        out->total_ms = el(0, 3 * nsteps + 1);
         if (eerr != cudaSuccess) {
             cudaGetLastError();
             return fail(h, DPD_ERR_STATE, std::string("event timing unavailable: ") + cudaGetErrorString(eerr));
@@ -903,17 +910,14 @@ dpd_status dpd_observables(dpd_sim *h, dpd_obs *out)
     dpd_status st = guard(h, true);
     if (st) return st;
     if (!out) return fail(h, DPD_ERR_ARG, "out is NULL");
-    const int nb = observe_blocks_for((int)h->n);
+    const int nb = observe_blocks_for(h->P.ngroups);
     CUDA_TRY(h, launch_observe(h->P, h->D, nb, h->stream));
-    std::vector<double> part((size_t)nb * 8);
-    CUDA_TRY(h, cudaMemcpyAsync(part.data(), h->D.red, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, h->stream));
+    double acc[8];
+    CUDA_TRY(h, cudaMemcpyAsync(acc, h->D.red + (size_t)nb * 8, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
     DevCtl c;
     CUDA_TRY(h, cudaMemcpyAsync(&c, h->D.ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
     st = wait(h);
     if (st) return st;
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nb; ++b)
-        for (int k = 0; k < 8; ++k) acc[k] += part[(size_t)b * 8 + k];
     const double V = h->box[0] * h->box[1] * h->box[2];
     out->step = c.step;
     out->n = h->n;

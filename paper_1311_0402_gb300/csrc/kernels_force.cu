@@ -495,49 +495,33 @@ __device__ void block_reduce8(double (&v)[8], double *out)
     }
 }
 
-// Per-block partial sums of: sum v^2, sum v (3), and the conservative +
-// bond virial sum_{i<j} r_ij . F_ij (each pair seen from both ends, halved).
+// Observables, per-block partials of: sum v^2, sum v (3), and the virial
+// sum over pairs inside r_c of r_ij . F^C_ij plus the bonds' share (Eq. 3
+// and Sec. 4.5).  One warp per group: the kinetic terms of its owners, their
+// bonds (each bond seen from both ends, halved), then the group's packed
+// list 32 entries at a time -- every pair inside r_c is listed (no particle
+// has moved more than skin/2 since the build), once in Newton-3 mode and
+// from both ends otherwise, hence the pair weight.  Every sum runs in a
+// fixed order.
 template <bool ONE_SPECIES>
 __global__ void __launch_bounds__(kThreads) k_observe(SimParams P, Ptrs D)
 {
     const uint32_t par = D.ctl->parity;
-    const float4 *pos = D.pos[par];
-    const float4 *vel = D.vel[par];
+    const float4 *__restrict__ pos = D.pos[par];
+    const float4 *__restrict__ vel = D.vel[par];
+    const int lane = threadIdx.x & 31;
+    const uint32_t gid = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const uint2 desc = gid < (uint32_t)P.ngroups ? D.gdesc[gid] : make_uint2(0u, 0u);
+    const uint32_t owners = desc.y & 63u, nent = desc.y >> 6;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < P.n) {
-        float4 v = vel[i];
+    double vir = 0.0;
+    if ((uint32_t)lane < owners) {
+        const uint32_t i = desc.x + lane;
+        const float4 v = vel[i];
         acc[0] = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
         acc[1] = v.x; acc[2] = v.y; acc[3] = v.z;
-        float4 pi = pos[i];
-        const int ti = __float_as_int(pi.w);
-        // pairs inside r_c from the cell list (27 surrounding cells of the
-        // last build; cells are at least r_list wide and no particle has
-        // moved more than skin/2 since), independent of the row format
-        const int cx = min(max((int)(pi.x * P.cells_per_len[0]), 0), P.nc[0] - 1);
-        const int cy = min(max((int)(pi.y * P.cells_per_len[1]), 0), P.nc[1] - 1);
-        const int cz = min(max((int)(pi.z * P.cells_per_len[2]), 0), P.nc[2] - 1);
-        const uint32_t c = D.rank_of_cell[(cz * P.nc[1] + cy) * P.nc[0] + cx];
-        double vir = 0.0;
-        for (int sidx = 0; sidx < kStencil; ++sidx) {
-            const uint32_t cc = D.stencil[(size_t)c * kStencil + sidx];
-            if (cc == kNone) break;
-            for (uint32_t j = D.cell_start[cc]; j < D.cell_start[cc + 1]; ++j) {
-                if (j == (uint32_t)i) continue;
-                float4 pj = pos[j];
-                float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-                float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-                float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-                float d2 = dist2_rn(dx, dy, dz);
-                if (d2 < P.rc2 && d2 > 0.0f) {
-                    float r = sqrtf(d2);
-                    float w = fmaxf(1.0f - r * P.inv_rc, 0.0f);
-                    float a = ONE_SPECIES ? P.a[0] : P.a[ti * P.n_species + __float_as_int(pj.w)];
-                    vir += 0.5 * (double)(a * w * r);
-                }
-            }
-        }
         if (P.has_bonds) {
+            const float4 pi = pos[i];
             const uint32_t *bp = D.bond_partner + (size_t)D.pid[D.ctl->oparity][i] * kMaxBonds;
             for (int b = 0; b < kMaxBonds && bp[b] != kNone; ++b) {
                 float4 pj = pos[D.idx_of_pid[bp[b]]];
@@ -548,9 +532,36 @@ __global__ void __launch_bounds__(kThreads) k_observe(SimParams P, Ptrs D)
                 vir += 0.5 * (double)(-P.k_bond * (r - P.r0_bond) * r);
             }
         }
-        acc[4] = vir;
     }
+    const double wpair = P.newton3 ? 1.0 : 0.5;
+    const uint32_t *__restrict__ list = D.nbr + (size_t)gid * P.gcap;
+    for (uint32_t k = (uint32_t)lane; k < nent; k += 32u) {
+        const uint32_t e = list[k];
+        const float4 pi = pos[desc.x + (e >> kOwnerShift)];
+        const float4 pj = pos[e & kIndexMask];
+        const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+        const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+        const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+        const float d2 = dist2_rn(dx, dy, dz);
+        if (d2 < P.rc2 && d2 > 0.0f) {
+            const float r = sqrtf(d2);
+            const float w = fmaxf(1.0f - r * P.inv_rc, 0.0f);
+            const float a = ONE_SPECIES ? P.a[0] : P.a[__float_as_int(pi.w) * P.n_species + __float_as_int(pj.w)];
+            vir += wpair * (double)(a * w * r);
+        }
+    }
+    acc[4] = vir;
     block_reduce8(acc, D.red + (size_t)blockIdx.x * 8);
+}
+
+// Sum of nb per-block partials (8 each) in a fixed order into out[0..7].
+__global__ void __launch_bounds__(kThreads) k_reduce8(const double *part, int nb, double *out)
+{
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += part[(size_t)b * 8 + k];
+    block_reduce8(acc, out);
 }
 
 // Binned profile: block b handles particles [b*chunk, (b+1)*chunk); thread t
@@ -621,11 +632,13 @@ cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream
 }
 
 template <bool ONE>
-cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, cudaStream_t s)
+cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, cudaStream_t s, cudaEvent_t after_pair,
+                           unsigned int ev_flags)
 {
     if (P.newton3) {
         // pair kernel (accumulation only), then the settle kernel of the mode
         cudaError_t e = launch_force_m<ONE, kForceEval, true, true>(P, D, of, s);
+        if (e == cudaSuccess && after_pair) e = cudaEventRecordWithFlags(after_pair, s, ev_flags);
         if (e != cudaSuccess) return e;
         // one thread per particle: the kernel streams memory and needs every
         // load in flight at once
@@ -647,6 +660,7 @@ cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, 
         else
             e = mode == kForceStep ? launch_force_m<ONE, kForceStep, false, false>(P, D, of, s)
                                    : launch_force_m<ONE, kForceFinish, false, false>(P, D, of, s);
+        if (e == cudaSuccess && after_pair) e = cudaEventRecordWithFlags(after_pair, s, ev_flags);
         if (e != cudaSuccess) return e;
     }
     if (mode == kForceStep) k_advance<true, true><<<1, 1, 0, s>>>(P, D);
@@ -662,7 +676,7 @@ int max_brick_cap() { return kMaxDynSmem / (2 * (int)sizeof(float4)); }
 
 cudaError_t init_kernel_attributes() { return init_build_attributes(kMaxDynSmem); }
 
-int observe_blocks_for(int n) { return (n + kThreads - 1) / kThreads; }
+int observe_blocks_for(int ngroups) { return (ngroups + kThreads / 32 - 1) / (kThreads / 32); }
 
 cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s)
 {
@@ -681,10 +695,11 @@ cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s)
+cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s,
+                         cudaEvent_t after_pair, unsigned int ev_flags)
 {
-    if (P.n_species == 1) return launch_force_s<true>(P, D, mode, out_fout ? 1 : 0, s);
-    return launch_force_s<false>(P, D, mode, out_fout ? 1 : 0, s);
+    if (P.n_species == 1) return launch_force_s<true>(P, D, mode, out_fout ? 1 : 0, s, after_pair, ev_flags);
+    return launch_force_s<false>(P, D, mode, out_fout ? 1 : 0, s, after_pair, ev_flags);
 }
 
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s)
@@ -693,6 +708,7 @@ cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaS
         k_observe<true><<<nblocks, kThreads, 0, s>>>(P, D);
     else
         k_observe<false><<<nblocks, kThreads, 0, s>>>(P, D);
+    k_reduce8<<<1, kThreads, 0, s>>>(D.red, nblocks, D.red + (size_t)nblocks * 8);
     return cudaGetLastError();
 }
 

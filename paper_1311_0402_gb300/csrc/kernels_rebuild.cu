@@ -16,10 +16,10 @@
 //              so the particle order and the lists are deterministic
 //   k_gather   permute the particle arrays into the other buffer set
 //   k_commit   flip the live buffer set
-//   k_nbuild   one thread per particle walks the 27 stencil cells in
-//              ascending rank order, so every list is strictly increasing
-//              (the property of the paper's builder, obtained here without
-//              warp votes because each thread owns its particle's row)
+//   k_nbuild_brick / k_nbuild
+//              packed neighbour lists of groups of 32 particles, hits
+//              compacted by warp ballots as in the paper's builder (Sec. 3.3);
+//              the list order depends only on the positions
 #include "dpd_internal.cuh"
 #include "dpd_math.cuh"
 #include "brick.cuh"
@@ -210,14 +210,22 @@ __global__ void k_gather(SimParams P, Ptrs D)
             D.xref[p] = x;
             D.vel[t][p] = D.vel[s][i];
             if (!LHALF) D.vkick[t][p] = D.vkick[s][i];
-            D.force[t][p] = D.force[s][i];
+            // force[] is not carried: every reader finds it rewritten first
+            // (a force evaluation, or the last step of a run)
             D.tag[ot][p] = D.tag[os][i];
             uint32_t id = D.pid[os][i];
             D.pid[ot][p] = id;
-            D.idx_of_pid[id] = (uint32_t)p;
+            if (P.has_bonds) D.idx_of_pid[id] = (uint32_t)p;  // bond partners are found by caller index
         }
         if (p < P.ncell) D.cell_count[p] = 0u;
     }
+}
+
+// idx_of_pid of the live order (when bonds are first set)
+__global__ void k_index(SimParams P, Ptrs D)
+{
+    const uint32_t *pid = D.pid[D.ctl->oparity];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n; p += gridDim.x * blockDim.x) D.idx_of_pid[pid[p]] = (uint32_t)p;
 }
 
 __global__ void k_commit(Ptrs D)
@@ -366,11 +374,59 @@ struct CellSeq {
     uint8_t head[32];
 };
 
+// One chunk against the owners [p_lo, p_hi) of cell slot t, kOwnersPerPass
+// owners at a time: every ballot of the pass over the NS live slots first
+// (no branches between them, so the tests overlap), then each owner's hits
+// are appended in turn, so an owner's entries stay contiguous in the list.
+constexpr int kOwnersPerPass = 1;
+
+template <bool WRAP, bool STAGED, bool HALF, int NS>
+__device__ __forceinline__ uint32_t owner_pass(const SimParams &P, const float4 *__restrict__ pos,
+                                               const float4 *s_pos, const uint32_t *s_off, const float4 (&cand)[kSlots],
+                                               int t, uint32_t g_own, uint32_t p_lo, uint32_t p_hi, uint32_t c0,
+                                               uint32_t c1, uint32_t first, uint32_t lane, uint32_t *list,
+                                               uint32_t gcap, uint32_t total)
+{
+    constexpr int NO = kOwnersPerPass;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t p = p_lo; p < p_hi; p += (uint32_t)NO) {
+        uint32_t m[NO][NS];
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+            const bool live = p + (uint32_t)o < p_hi;
+            const uint32_t po = live ? p + (uint32_t)o : p;
+            const uint32_t io = g_own + po;
+            const float4 pio = STAGED ? s_pos[s_off[t] + po] : pos[io];
+            const uint32_t k0 = HALF ? max(po + 1u, c0) : c0;
+#pragma unroll
+            for (int sl = 0; sl < NS; ++sl) {
+                const uint32_t k = c0 + 32u * sl + lane;
+                const uint32_t j = __float_as_uint(cand[sl].w);
+                m[o][sl] = __ballot_sync(0xFFFFFFFFu, live & (k < c1) & (k >= k0) & within_list<WRAP>(P, cand[sl], pio) &
+                                                          (HALF || j != io));
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+            const uint32_t entry_owner = (g_own + p + (uint32_t)o - first) << kOwnerShift;
+#pragma unroll
+            for (int sl = 0; sl < NS; ++sl) {
+                if ((m[o][sl] >> lane) & 1u) {
+                    const uint32_t q = total + (uint32_t)__popc(m[o][sl] & lt);
+                    if (q < gcap) list[q] = entry_owner | __float_as_uint(cand[sl].w);
+                }
+                total += (uint32_t)__popc(m[o][sl]);
+            }
+        }
+    }
+    return total;
+}
+
 // The owners [p_lo, p_hi) (places in cell slot t) of a group whose first
 // particle is `first`: their pairs with the candidate sequence, appended to
 // the group list; returns the new running total.  A chunk of kChunk
 // candidates is held in registers, lane l holding entries c0 + 32 s + l;
-// every owner of the cell tests against the same registers.
+// every owner of the cell tests against the same registers (owner_pass).
 template <bool WRAP, bool STAGED, bool HALF>
 __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 *__restrict__ pos,
                                                const float4 *s_pos, const uint32_t *s_off, const uint32_t *s_gstart,
@@ -434,50 +490,15 @@ __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 
                 }
             }
         }
-        // owners two at a time: all ballots first (independent work), then
-        // each owner's hits are appended in turn, so an owner's entries stay
-        // contiguous in the list
-        for (uint32_t p = p_lo; p < p_hi; p += 2u) {
-            const bool two = p + 1u < p_hi;
-            const uint32_t ia = g_own + p, ib = ia + (two ? 1u : 0u);
-            const float4 pa = STAGED ? s_pos[s_off[t] + p] : pos[ia];
-            const float4 pb = STAGED ? s_pos[s_off[t] + (ib - g_own)] : pos[ib];
-            const uint32_t k0a = HALF ? max(p + 1u, c0) : c0;
-            const uint32_t k0b = HALF ? max(p + 2u, c0) : c0;
-            uint32_t ma[kSlots], mb[kSlots];
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl) {
-                const uint32_t kb = c0 + 32u * sl;
-                ma[sl] = 0u;
-                mb[sl] = 0u;
-                if (kb < c1 && kb + 32u > k0a) {
-                    const uint32_t k = kb + lane;
-                    const uint32_t j = __float_as_uint(cand[sl].w);
-                    const bool in = k < c1;
-                    ma[sl] = __ballot_sync(0xFFFFFFFFu, in & (k >= k0a) & within_list<WRAP>(P, cand[sl], pa) &
-                                                            (HALF || j != ia));
-                    mb[sl] = __ballot_sync(0xFFFFFFFFu, two & in & (k >= k0b) & within_list<WRAP>(P, cand[sl], pb) &
-                                                            (HALF || j != ib));
-                }
-            }
-            const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl) {
-                if ((ma[sl] >> lane) & 1u) {
-                    const uint32_t q = total + (uint32_t)__popc(ma[sl] & lt);
-                    if (q < gcap) list[q] = ((ia - first) << kOwnerShift) | __float_as_uint(cand[sl].w);
-                }
-                total += (uint32_t)__popc(ma[sl]);
-            }
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl) {
-                if ((mb[sl] >> lane) & 1u) {
-                    const uint32_t q = total + (uint32_t)__popc(mb[sl] & lt);
-                    if (q < gcap) list[q] = ((ib - first) << kOwnerShift) | __float_as_uint(cand[sl].w);
-                }
-                total += (uint32_t)__popc(mb[sl]);
-            }
-        }
+        const uint32_t ns = (c1 - c0 + 31u) / 32u;  // live slots of this chunk
+        if (ns == 4u)
+            total = owner_pass<WRAP, STAGED, HALF, 4>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
+        else if (ns == 3u)
+            total = owner_pass<WRAP, STAGED, HALF, 3>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
+        else if (ns == 2u)
+            total = owner_pass<WRAP, STAGED, HALF, 2>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
+        else
+            total = owner_pass<WRAP, STAGED, HALF, 1>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
     }
     return total;
 }
@@ -571,6 +592,12 @@ int scan_blocks_for(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 cudaError_t init_build_attributes(int max_dyn_smem)
 {
     return cudaFuncSetAttribute(k_nbuild_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+}
+
+cudaError_t launch_index(const SimParams &P, const Ptrs &D, cudaStream_t s)
+{
+    k_index<<<grid_for(P.n), kThreads, 0, s>>>(P, D);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, int n_scan_blocks)
