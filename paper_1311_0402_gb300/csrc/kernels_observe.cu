@@ -1,0 +1,193 @@
+// kernels_observe.cu -- observables of the live state: kinetic sums and
+// the virial (Eq. 3 pressure), binned velocity profiles (Sec. 4.2), and the
+// pair random numbers exported for checking (Sec. 3.5).  None of these runs
+// inside the stepping graphs.
+#include "dpd_internal.cuh"
+#include "dpd_math.cuh"
+
+namespace dpd {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Deterministic block reduction of 8 doubles (fixed shuffle tree, then a
+// fixed order over the warps); thread 0 writes the block's partials.
+__device__ void block_reduce8(double (&v)[8], double *out)
+{
+    __shared__ double sh[8][kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) sh[k][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += sh[threadIdx.x][w];
+        out[threadIdx.x] = s;
+    }
+}
+
+// Observables, per-block partials of: sum v^2, sum v (3), and the virial
+// sum over pairs inside r_c of r_ij . F^C_ij plus the bonds' share (Eq. 3
+// and Sec. 4.5).  Each warp takes groups in turn: the kinetic terms of the owners, their
+// bonds (each bond seen from both ends, halved), then the group's packed
+// list 32 entries at a time -- every pair inside r_c is listed (no particle
+// has moved more than skin/2 since the build), once in Newton-3 mode and
+// from both ends otherwise, hence the pair weight.  Every sum runs in a
+// fixed order.
+template <bool ONE_SPECIES>
+__global__ void __launch_bounds__(kThreads) k_observe(SimParams P, Ptrs D)
+{
+    const uint32_t par = D.ctl->parity;
+    const float4 *__restrict__ pos = D.pos[par];
+    const float4 *__restrict__ vel = D.vel[par];
+    const int lane = threadIdx.x & 31;
+    constexpr uint32_t W = kThreads / 32;
+    // FP64 arithmetic is scarce on this part: the kinetic sums (exact
+    // squares of FP32 values) use it once per particle, the pair virial is
+    // accumulated per lane in FP32 and converted once per group
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float wpair = P.newton3 ? 1.0f : 0.5f;
+    for (uint32_t gid = blockIdx.x * W + (threadIdx.x >> 5); gid < (uint32_t)P.ngroups; gid += gridDim.x * W) {
+        const uint2 desc = D.gdesc[gid];
+        const uint32_t owners = desc.y & 63u, nent = desc.y >> 6;
+        if ((uint32_t)lane < owners) {
+            const uint32_t i = desc.x + lane;
+            const float4 v = vel[i];
+            const double vx = v.x, vy = v.y, vz = v.z;
+            acc[0] += vx * vx + vy * vy + vz * vz;
+            acc[1] += vx; acc[2] += vy; acc[3] += vz;
+            if (P.has_bonds) {
+                const float4 pi = pos[i];
+                const uint32_t *bp = D.bond_partner + (size_t)D.pid[D.ctl->oparity][i] * kMaxBonds;
+                float vb = 0.0f;
+                for (int b = 0; b < kMaxBonds && bp[b] != kNone; ++b) {
+                    float4 pj = pos[D.idx_of_pid[bp[b]]];
+                    float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+                    float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+                    float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+                    float r = sqrtf(dx * dx + dy * dy + dz * dz);
+                    vb += 0.5f * (-P.k_bond * (r - P.r0_bond) * r);
+                }
+                acc[4] += (double)vb;
+            }
+        }
+        const uint32_t *__restrict__ list = D.nbr + (size_t)gid * P.gcap;
+        float vir = 0.0f;
+        for (uint32_t k = (uint32_t)lane; k < nent; k += 32u) {
+            const uint32_t e = list[k];
+            const float4 pi = pos[desc.x + (e >> kOwnerShift)];
+            const float4 pj = pos[e & kIndexMask];
+            const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+            const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+            const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+            const float d2 = dist2_rn(dx, dy, dz);
+            if (d2 < P.rc2 && d2 > 0.0f) {
+                const float r = sqrtf(d2);
+                const float w = fmaxf(1.0f - r * P.inv_rc, 0.0f);
+                const float a = ONE_SPECIES ? P.a[0] : P.a[__float_as_int(pi.w) * P.n_species + __float_as_int(pj.w)];
+                vir = fmaf(wpair, a * w * r, vir);
+            }
+        }
+        acc[4] += (double)vir;
+    }
+    block_reduce8(acc, D.red + (size_t)blockIdx.x * 8);
+}
+
+// Sum of nb per-block partials (8 each) in a fixed order into out[0..7].
+__global__ void __launch_bounds__(kThreads) k_reduce8(const double *part, int nb, double *out)
+{
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += part[(size_t)b * 8 + k];
+    block_reduce8(acc, out);
+}
+
+// Binned profile: block b handles particles [b*chunk, (b+1)*chunk); thread t
+// owns bins t, t + blockDim, ... and scans the chunk in order, so every
+// partial is summed in a fixed order.  Partials: red[b][2*nbins].
+__global__ void __launch_bounds__(kThreads) k_profile(SimParams P, Ptrs D, int bin_axis, int vel_axis, int nbins,
+                                                     int chunk)
+{
+    const uint32_t par = D.ctl->parity;
+    const float4 *pos = D.pos[par];
+    const float4 *vel = D.vel[par];
+    const int b0 = blockIdx.x * chunk;
+    const int b1 = min(P.n, b0 + chunk);
+    const float scale = (float)nbins / P.L[bin_axis];
+    double *out = D.red + (size_t)blockIdx.x * 2 * nbins;
+    for (int bin = threadIdx.x; bin < nbins; bin += blockDim.x) {
+        double s = 0.0, c = 0.0;
+        for (int p = b0; p < b1; ++p) {
+            float4 x = pos[p];
+            float xc = bin_axis == 0 ? x.x : (bin_axis == 1 ? x.y : x.z);
+            int bb = (int)(xc * scale);
+            bb = bb < 0 ? 0 : (bb >= nbins ? nbins - 1 : bb);
+            if (bb == bin) {
+                float4 v = vel[p];
+                s += vel_axis == 0 ? v.x : (vel_axis == 1 ? v.y : v.z);
+                c += 1.0;
+            }
+        }
+        out[2 * bin] = s;
+        out[2 * bin + 1] = c;
+    }
+}
+
+__global__ void k_pair_rng(uint64_t seed, uint32_t step, int64_t m, const uint32_t *ti, const uint32_t *tj,
+                           uint32_t *out_hash, float *out_xi)
+{
+    const uint32_t key[4] = {(uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32), 0x243F6A88u, 0x85A308D3u};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t si = signature(ti[k], step, key);
+        uint32_t sj = signature(tj[k], step, key);
+        uint32_t A, B;
+        pair_hash(si, sj, key, A, B);
+        out_hash[2 * k] = A;
+        out_hash[2 * k + 1] = B;
+        if (out_xi) out_xi[k] = gauss_from_hash(A, B);
+    }
+}
+
+}  // namespace
+
+int observe_blocks_for(int ngroups)
+{
+    const int g = (ngroups + kThreads / 32 - 1) / (kThreads / 32);
+    return g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g);  // grid-stride beyond 8 blocks per SM
+}
+
+cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s)
+{
+    if (P.n_species == 1)
+        k_observe<true><<<nblocks, kThreads, 0, s>>>(P, D);
+    else
+        k_observe<false><<<nblocks, kThreads, 0, s>>>(P, D);
+    k_reduce8<<<1, kThreads, 0, s>>>(D.red, nblocks, D.red + (size_t)nblocks * 8);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int vel_axis, int nbins, int nblocks,
+                           cudaStream_t s)
+{
+    const int chunk = (P.n + nblocks - 1) / nblocks;
+    k_profile<<<nblocks, kThreads, 0, s>>>(P, D, bin_axis, vel_axis, nbins, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *ti, const uint32_t *tj,
+                            uint32_t *out_hash, float *out_xi, cudaStream_t s)
+{
+    int64_t g = (m + kThreads - 1) / kThreads;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    k_pair_rng<<<(int)g, kThreads, 0, s>>>(seed, (uint32_t)step, m, ti, tj, out_hash, out_xi);
+    return cudaGetLastError();
+}
+
+}  // namespace dpd
