@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-boxes", type=int, default=512)
+    ap.add_argument("--serve-active", type=int, default=32)
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -195,6 +198,69 @@ def run_reference(args):
     return 0
 
 
+def run_serving(args):
+    """Batched serving leg: the seeded stream of independent boxes (L in 6..30,
+    rho = 3, a in [15, 40], gamma in [3, 6], 500-5000 steps) run (1) one box at
+    a time through the plain path, (2) all submitted at once to the serving
+    loop, (3) submitted at Poisson arrival times, 1.2x the one-box-at-a-time
+    capacity, for p50 / p99 time-to-completion."""
+    import paper_1311_0402_gb300 as dpd
+    import workloads
+    boxes = workloads.serving_stream(args.serve_boxes, with_state=True)
+    total = float(sum(b["n"] * b["steps"] for b in boxes))
+    # (1) one box at a time, plain path: create, load, step, read back, free
+    t0 = time.perf_counter()
+    for b in boxes:
+        sim = dpd.Sim(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], seed=b["seed"])
+        sim.set_state(b["x"], b["v"])
+        sim.step(b["steps"])
+        sim.observables()
+        sim.state()
+        sim.close()
+    t_seq = time.perf_counter() - t0
+
+    def submit(srv, b):
+        return srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
+                          b["steps"], seed=b["seed"])
+
+    # (2) saturated: everything queued at once
+    srv = dpd.Server(max_active=args.serve_active, chunk_steps=100)
+    t0 = srv.now()
+    tickets = [submit(srv, b) for b in boxes]
+    res = [srv.wait(t, timeout_s=3600.0, state=True) for t in tickets]
+    t_sat = max(r["t_done"] for r in res) - t0
+    bad = sum(1 for r in res if r["status"] != 0)
+    srv.close()
+    # (3) Poisson arrivals at 1.2x the one-box-at-a-time capacity
+    rate = 1.2 * len(boxes) / t_seq
+    arrivals = workloads.serving_stream(args.serve_boxes, with_state=False, rate=rate)
+    srv = dpd.Server(max_active=args.serve_active, chunk_steps=100)
+    t0 = srv.now()
+    tickets = []
+    for b, a in zip(boxes, arrivals):
+        dt = a["t_arrive"] - (srv.now() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(submit(srv, b))
+    res = [srv.wait(t, timeout_s=3600.0, state=False) for t in tickets]
+    srv.close()
+    bad += sum(1 for r in res if r["status"] != 0)
+    ttc = np.array([r["t_done"] - r["t_submit"] for r in res])
+    span = max(r["t_done"] for r in res) - t0
+    return {
+        "metric": "batched-ensemble time-to-completion (p50 / p99) and particle-steps/s",
+        "boxes": len(boxes), "particle_steps": total, "failed": bad,
+        "workload": "seeded stream of independent periodic cubes, L uniform in 6..30, rho=3 (648..81000 "
+                    "particles), a in [15,40], gamma in [3,6], kT=1, dt=0.01, 500-5000 steps each",
+        "one_box_at_a_time": {"value": total / t_seq, "unit": UNIT, "wall_s": t_seq},
+        "saturated": {"value": total / t_sat, "unit": UNIT, "wall_s": t_sat,
+                      "vs_one_box_at_a_time": t_seq / t_sat, "max_active": args.serve_active},
+        "poisson": {"rate_boxes_per_s": rate, "value": total / span, "unit": UNIT, "wall_s": span,
+                    "p50_s": float(np.percentile(ttc, 50)), "p99_s": float(np.percentile(ttc, 99)),
+                    "arrival": "Poisson, 1.2x the one-box-at-a-time capacity"},
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -323,6 +389,8 @@ def main():
                                 "sample": "FP64 oracle (single-threaded C), %d steps of the full %d-particle box "
                                           "(%.1f s)" % (sample_steps, n, secs)}
     sim.close()
+    if rank == 0 and ws == 1 and not args.no_serving:
+        line["batched"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -156,6 +156,17 @@ dpd_status dpd_set_force(dpd_sim *h, const double *f);
  * is then unreliable; reload it with dpd_set_state). */
 dpd_status dpd_step(dpd_sim *h, int64_t nsteps);
 
+/* dpd_step split in two, for overlapping several handles (each on its own
+ * stream) from one host thread: dpd_step_async queues nsteps on the handle's
+ * stream and returns at once; dpd_sync waits for everything queued and
+ * reports a device error of any queued run (overflow, non-finite force,
+ * staging timeout), as dpd_step does; dpd_query sets *idle = 1 when the
+ * handle's stream has finished all queued work (no wait).  Other calls that
+ * read the state wait for queued steps first (stream order). */
+dpd_status dpd_step_async(dpd_sim *h, int64_t nsteps);
+dpd_status dpd_sync(dpd_sim *h);
+dpd_status dpd_query(dpd_sim *h, int32_t *idle);
+
 /* Per-phase device times of a run, measured with CUDA events recorded on
  * the handle's stream around every kernel group of every step. */
 typedef struct {

@@ -25,7 +25,11 @@ STATUS = {0: "DPD_OK", 1: "DPD_ERR_ARG", 2: "DPD_ERR_OOM", 3: "DPD_ERR_CUDA", 4:
 EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds", "dpd_build_neighbors",
            "dpd_get_neighbors", "dpd_forces", "dpd_get_force", "dpd_step", "dpd_observables", "dpd_profile",
            "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled",
-           "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error", "dpd_set_force")
+           "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error", "dpd_set_force",
+           "dpd_step_async", "dpd_sync", "dpd_query",
+           # include/dpd_server.h
+           "dpd_server_default_options", "dpd_server_create", "dpd_server_submit", "dpd_server_wait",
+           "dpd_server_now", "dpd_server_counts", "dpd_server_last_error", "dpd_server_destroy")
 
 
 class DPDError(RuntimeError):
@@ -60,6 +64,47 @@ class dpd_obs(ctypes.Structure):
         ("virial", ctypes.c_double),
         ("pressure", ctypes.c_double),
         ("momentum", ctypes.c_double * 3),
+    ]
+
+
+class dpd_server_options(ctypes.Structure):
+    _fields_ = [
+        ("max_active", ctypes.c_int32),
+        ("chunk_steps", ctypes.c_int32),
+        ("mem_budget_bytes", ctypes.c_double),
+        ("box_options", dpd_options),
+    ]
+
+
+class dpd_request(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double * 3),
+        ("n_species", ctypes.c_int32),
+        ("a_ij", ctypes.POINTER(ctypes.c_double)),
+        ("gamma", ctypes.c_double),
+        ("kT", ctypes.c_double),
+        ("rc", ctypes.c_double),
+        ("s", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("n", ctypes.c_int64),
+        ("x", ctypes.POINTER(ctypes.c_double)),
+        ("v", ctypes.POINTER(ctypes.c_double)),
+        ("species", ctypes.POINTER(ctypes.c_int32)),
+        ("steps", ctypes.c_uint64),
+    ]
+
+
+class dpd_result(ctypes.Structure):
+    _fields_ = [
+        ("ticket", ctypes.c_uint64),
+        ("status", ctypes.c_int32),
+        ("n", ctypes.c_int64),
+        ("steps", ctypes.c_uint64),
+        ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+        ("obs", dpd_obs),
     ]
 
 
@@ -137,6 +182,21 @@ def lib():
         L.dpd_forces_static_last_error.restype = ctypes.c_char_p
         L.dpd_destroy.argtypes = [vp]
         L.dpd_destroy.restype = None
+        L.dpd_step_async.argtypes = [vp, i64]
+        L.dpd_sync.argtypes = [vp]
+        L.dpd_query.argtypes = [vp, P(i32)]
+        L.dpd_server_default_options.argtypes = [P(dpd_server_options)]
+        L.dpd_server_default_options.restype = None
+        L.dpd_server_create.argtypes = [P(dpd_server_options), P(vp)]
+        L.dpd_server_submit.argtypes = [vp, P(dpd_request), P(u64)]
+        L.dpd_server_wait.argtypes = [vp, u64, f64, P(dpd_result), P(f64), P(f64)]
+        L.dpd_server_now.argtypes = [vp]
+        L.dpd_server_now.restype = f64
+        L.dpd_server_counts.argtypes = [vp, P(i64), P(i64), P(i64), P(f64)]
+        L.dpd_server_last_error.argtypes = [vp]
+        L.dpd_server_last_error.restype = ctypes.c_char_p
+        L.dpd_server_destroy.argtypes = [vp]
+        L.dpd_server_destroy.restype = None
         _lib = L
     return _lib
 
@@ -223,6 +283,20 @@ def dpd_set_force(h, f):
 
 def dpd_step(h, nsteps: int):
     _check(lib().dpd_step(h, int(nsteps)), h)
+
+
+def dpd_step_async(h, nsteps: int):
+    _check(lib().dpd_step_async(h, int(nsteps)), h)
+
+
+def dpd_sync(h):
+    _check(lib().dpd_sync(h), h)
+
+
+def dpd_query(h) -> bool:
+    idle = ctypes.c_int32(0)
+    _check(lib().dpd_query(h, ctypes.byref(idle)), h)
+    return bool(idle.value)
 
 
 def dpd_step_profiled(h, nsteps: int) -> dict:
@@ -363,6 +437,15 @@ class Sim:
     def step(self, n):
         dpd_step(self.h, n)
 
+    def step_async(self, n):
+        dpd_step_async(self.h, n)
+
+    def sync(self):
+        dpd_sync(self.h)
+
+    def query(self) -> bool:
+        return dpd_query(self.h)
+
     def step_profiled(self, n):
         return dpd_step_profiled(self.h, n)
 
@@ -377,3 +460,88 @@ class Sim:
 
     def info(self):
         return dpd_info(self.h)
+
+
+# ------------------------------------------------------------ serving loop
+def _server_check(st, srv):
+    if st != DPD_OK:
+        m = lib().dpd_server_last_error(srv)
+        raise DPDError(st, m.decode() if m else "")
+
+
+class Server:
+    """Continuous batching of independent boxes (include/dpd_server.h)."""
+
+    def __init__(self, max_active=32, chunk_steps=100, mem_budget_bytes=0.0, skin=0.3, deterministic=0,
+                 graph_steps=8, lam=0.5):
+        o = dpd_server_options()
+        lib().dpd_server_default_options(ctypes.byref(o))
+        o.max_active = max_active
+        o.chunk_steps = chunk_steps
+        o.mem_budget_bytes = float(mem_budget_bytes)
+        o.box_options.skin = skin
+        o.box_options.deterministic = 1 if deterministic else 0
+        o.box_options.graph_steps = graph_steps
+        o.box_options.lam = lam
+        self.s = ctypes.c_void_p()
+        _server_check(lib().dpd_server_create(ctypes.byref(o), ctypes.byref(self.s)), None)
+        self._n = {}
+
+    def submit(self, box, a_ij, gamma, kT, rc, s, dt, x, v, steps, seed=42, species=None) -> int:
+        a = np.ascontiguousarray(np.atleast_2d(np.asarray(a_ij, np.float64)))
+        x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+        v = np.ascontiguousarray(v, np.float64).reshape(-1, 3)
+        sp = None if species is None else np.ascontiguousarray(species, np.int32)
+        r = dpd_request()
+        r.box[:] = [float(b) for b in box]
+        r.n_species = a.shape[0]
+        r.a_ij = _p(a, ctypes.c_double)
+        r.gamma, r.kT, r.rc, r.s, r.dt = gamma, kT, rc, s, dt
+        r.seed = seed
+        r.n = x.shape[0]
+        r.x = _p(x, ctypes.c_double)
+        r.v = _p(v, ctypes.c_double)
+        r.species = _p(sp, ctypes.c_int32) if sp is not None else None
+        r.steps = int(steps)
+        t = ctypes.c_uint64()
+        _server_check(lib().dpd_server_submit(self.s, ctypes.byref(r), ctypes.byref(t)), self.s)
+        self._n[t.value] = x.shape[0]
+        return t.value
+
+    def wait(self, ticket, timeout_s=600.0, state=True):
+        n = self._n.get(ticket, 0)
+        state = state and n > 0
+        res = dpd_result()
+        x = np.zeros((n, 3), np.float64) if state else None
+        v = np.zeros((n, 3), np.float64) if state else None
+        _server_check(lib().dpd_server_wait(self.s, ticket, timeout_s, ctypes.byref(res), _p(x, ctypes.c_double),
+                                            _p(v, ctypes.c_double)), self.s)
+        self._n.pop(ticket, None)
+        o = res.obs
+        out = dict(ticket=res.ticket, status=res.status, n=res.n, steps=res.steps, t_submit=res.t_submit,
+                   t_admit=res.t_admit, t_done=res.t_done,
+                   obs=dict(step=o.step, n=o.n, kinetic=o.kinetic, temperature=o.temperature, virial=o.virial,
+                            pressure=o.pressure, momentum=np.array(list(o.momentum))))
+        if state:
+            out["x"], out["v"] = x, v
+        return out
+
+    def now(self) -> float:
+        return float(lib().dpd_server_now(self.s))
+
+    def counts(self):
+        q, r, f, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _server_check(lib().dpd_server_counts(self.s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f),
+                                              ctypes.byref(m)), self.s)
+        return dict(queued=q.value, running=r.value, finished=f.value, mem_bytes=m.value)
+
+    def close(self):
+        if self.s is not None and self.s.value:
+            lib().dpd_server_destroy(self.s)
+        self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

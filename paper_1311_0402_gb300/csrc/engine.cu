@@ -140,6 +140,7 @@ struct dpd_sim {
     std::map<int64_t, cudaGraphExec_t> timed_graphs;  // profiled runs, by steps
     std::vector<cudaEvent_t> tev;           // timing events
     uint64_t step = 0;                       // host mirror of the device step
+    bool pending = false;                    // steps queued by dpd_step_async not yet checked by dpd_sync
     std::string err;
     std::vector<uint32_t> bond_partner_host;
     bool bonds_set = false;
@@ -164,21 +165,47 @@ dpd_status fail(dpd_sim *h, dpd_status st, const std::string &msg)
             return fail((h), DPD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
     } while (0)
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// handle's stream, from the device's default pool): creating and destroying a
+// handle never synchronises the whole device, so handles on other streams
+// keep running (the serving loop relies on this).
+// Keep freed stream-ordered memory in this process's pool of the current
+// device instead of returning it at every synchronisation, so that handles
+// created after others were destroyed reuse it without new mappings.
+void keep_pool_memory()
+{
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    uint64_t threshold = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold) != cudaSuccess) cudaGetLastError();
+}
+
 dpd_status dev_alloc(dpd_sim *h, void **p, size_t bytes, std::vector<void *> &list)
 {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(h, DPD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        return fail(h, DPD_ERR_OOM, std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
     list.push_back(*p);
     return DPD_OK;
 }
 
-void free_list(std::vector<void *> &list)
+void dev_free(dpd_sim *h, void *p, std::vector<void *> &list)
 {
-    for (void *p : list) cudaFree(p);
+    auto it = std::find(list.begin(), list.end(), p);
+    if (it != list.end()) list.erase(it);
+    cudaFreeAsync(p, h->stream);
+}
+
+void free_list(dpd_sim *h, std::vector<void *> &list)
+{
+    for (void *p : list) cudaFreeAsync(p, h->stream);
     list.clear();
 }
 
@@ -326,7 +353,7 @@ int auto_capacity(const dpd_sim *h, int64_t n)
 dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
 {
     drop_graphs(h);
-    free_list(h->allocs);
+    free_list(h, h->allocs);
     Ptrs &D = h->D;
     const size_t f4 = sizeof(float4) * (size_t)n, u4 = sizeof(uint32_t) * (size_t)n;
     dpd_status st = DPD_OK;
@@ -382,8 +409,7 @@ dpd_status rebuild_and_force(dpd_sim *h, bool grow_on_overflow)
         const int cap = capacity_for_total(c.max_nnb);
         if ((int64_t)cap * kGroup >= (int64_t(1) << 26))
             return fail(h, DPD_ERR_NBR_OVERFLOW, "neighbour list overflow: group list beyond 2^26 entries");
-        cudaFree(h->D.nbr);
-        h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->D.nbr));
+        dev_free(h, h->D.nbr, h->allocs);
         st = dev_alloc(h, (void **)&h->D.nbr, (size_t)h->P.ngroups * kGroup * (size_t)cap * sizeof(uint32_t),
                        h->allocs);
         if (st) return st;
@@ -541,6 +567,7 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
         dpd_destroy(h);
         return fail(nullptr, DPD_ERR_CUDA, "cudaEventCreate failed");
     }
+    keep_pool_memory();
     build_geometry(nc, h->geo);
     h->n_scan_blocks = scan_blocks_for(P.ncell);
     P.use_bricks = (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3) ? 1 : 0;
@@ -646,6 +673,7 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
         }
     }
     h->has_state = false;
+    h->pending = false;
     h->bonds_set = false;
     h->P.has_bonds = 0;
     drop_graphs(h);
@@ -702,6 +730,7 @@ dpd_status dpd_build_neighbors(dpd_sim *h)
 {
     dpd_status st = guard(h, true);
     if (st) return st;
+    if (h->pending && (st = dpd_sync(h)) != DPD_OK) return st;  // report a queued run's error first
     return rebuild_and_force(h, h->opt.nbr_capacity == 0);
 }
 
@@ -750,6 +779,7 @@ dpd_status dpd_forces(dpd_sim *h, double *f_out)
 {
     dpd_status st = guard(h, true);
     if (st) return st;
+    if (h->pending && (st = dpd_sync(h)) != DPD_OK) return st;  // report a queued run's error first
     CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
     CUDA_TRY(h, launch_force(h->P, h->D, kForceEval, true, h->stream));
     DevCtl c;
@@ -795,13 +825,16 @@ dpd_status dpd_set_force(dpd_sim *h, const double *f)
     return wait(h);
 }
 
-dpd_status dpd_step(dpd_sim *h, int64_t nsteps)
+dpd_status dpd_step_async(dpd_sim *h, int64_t nsteps)
 {
     dpd_status st = guard(h, true);
     if (st) return st;
     if (nsteps < 0) return fail(h, DPD_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return DPD_OK;
-    CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+    // the error word is cleared only when no unchecked run is queued, so an
+    // error of an earlier chunk survives until dpd_sync reads it
+    if (!h->pending) CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+    h->pending = true;
     const int K = h->opt.graph_steps;
     int64_t left = nsteps;
     if (K > 0) {
@@ -822,13 +855,42 @@ dpd_status dpd_step(dpd_sim *h, int64_t nsteps)
         CUDA_TRY(h, enqueue_steps(h, (int)left));
     }
     h->step += (uint64_t)nsteps;
+    return DPD_OK;
+}
+
+dpd_status dpd_sync(dpd_sim *h)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
     DevCtl c;
     st = check_err(h, c);
-    if (st) {
-        h->has_state = st == DPD_ERR_TIMEOUT ? h->has_state : false;
-        return st;
+    if (st == DPD_ERR_TIMEOUT) return st;  // still running: the run stays pending
+    h->pending = false;
+    if (st) h->has_state = false;
+    return st;
+}
+
+dpd_status dpd_query(dpd_sim *h, int32_t *idle)
+{
+    if (!h || !idle) return fail(h, DPD_ERR_ARG, "null argument");
+    const cudaError_t e = cudaStreamQuery(h->stream);
+    if (e == cudaSuccess) {
+        *idle = 1;
+        return DPD_OK;
     }
-    return DPD_OK;
+    if (e == cudaErrorNotReady) {
+        *idle = 0;
+        return DPD_OK;
+    }
+    cudaGetLastError();
+    return fail(h, DPD_ERR_CUDA, std::string("kernel failure: ") + cudaGetErrorString(e));
+}
+
+dpd_status dpd_step(dpd_sim *h, int64_t nsteps)
+{
+    dpd_status st = dpd_step_async(h, nsteps);
+    if (st || nsteps == 0) return st;
+    return dpd_sync(h);
 }
 
 dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
@@ -836,6 +898,7 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
     dpd_status st = guard(h, true);
     if (st) return st;
     if (nsteps < 1 || nsteps > 100000) return fail(h, DPD_ERR_ARG, "nsteps must be in 1..100000");
+    if (h->pending && (st = dpd_sync(h)) != DPD_OK) return st;  // report a queued run's error first
     const size_t nev = (size_t)(3 * nsteps + 2);
     while (h->tev.size() < nev) {
         cudaEvent_t e;
@@ -945,8 +1008,7 @@ dpd_status dpd_profile(dpd_sim *h, int32_t bin_axis, int32_t vel_axis, int32_t n
         double *nr = nullptr;
         st = dev_alloc(h, (void **)&nr, need * sizeof(double), h->allocs);
         if (st) return st;
-        h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), (void *)h->D.red));
-        cudaFree(h->D.red);
+        dev_free(h, h->D.red, h->allocs);
         h->D.red = nr;
         h->red_doubles = need;
         drop_graphs(h);
@@ -1038,8 +1100,8 @@ void dpd_destroy(dpd_sim *h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
-    free_list(h->allocs);
-    free_list(h->static_allocs);
+    free_list(h, h->allocs);
+    free_list(h, h->static_allocs);
     for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     if (h->ev) cudaEventDestroy(h->ev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

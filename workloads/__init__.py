@@ -20,6 +20,10 @@ are the synthetic stand-ins, with the shapes and densities of those runs):
 * ``amphiphile``    -- periodic cube L = 64, rho = 3 (786,432 beads), species
   W/H/T, 10 % of the beads in H1T3 chains with harmonic bonds k = 100,
   r0 = 0.7, a_WW = a_HH = a_TT = a_WH = 25, a_WT = a_HT = 75, dt = 0.005.
+* ``serving_stream`` -- the batched-serving workload: a seeded Poisson
+  stream of independent periodic cubes, L uniform in 6..30 (integer),
+  rho = 3 (648 to 81,000 particles), a uniform in [15, 40], gamma uniform in
+  [3, 6], kT = 1, rc = 1, s = 1, dt = 0.01, 500-5000 steps each.
 """
 from __future__ import annotations
 
@@ -116,3 +120,30 @@ def amphiphile_state(box, n: int, kT: float, chain_fraction: float, r0: float, s
     b = np.arange(n_chain, dtype=np.uint32)[:, None] * 4 + np.arange(3, dtype=np.uint32)[None, :]
     bonds = np.stack([b.reshape(-1), b.reshape(-1) + 1], axis=1).astype(np.uint32)
     return x, v, species, bonds
+
+
+def serving_stream(nboxes: int, seed: int = BASE_SEED + 5, L_range=(6, 30), steps_range=(500, 5000),
+                   rate: float | None = None, with_state: bool = True):
+    """A list of independent boxes for the serving workload, each a dict with
+    box, a, gamma, kT, rc, s, dt, steps, seed (its random-force key) and, with
+    with_state, x and v; and, when rate (boxes per second) is given, Poisson
+    arrival times t_arrive (exponential gaps, first arrival at 0)."""
+    g = rng(seed)
+    out = []
+    t = 0.0
+    for k in range(nboxes):
+        L = float(g.integers(L_range[0], L_range[1] + 1))
+        a = float(g.uniform(15.0, 40.0))
+        gamma = float(g.uniform(3.0, 6.0))
+        steps = int(g.integers(steps_range[0], steps_range[1] + 1))
+        box = (L, L, L)
+        b = dict(box=box, a=[[a]], gamma=gamma, kT=1.0, rc=1.0, s=1.0, dt=0.01, lam=0.5, steps=steps,
+                 seed=int(TEA_SEED + k), n=n_particles(box, 3.0))
+        if rate is not None:
+            if k > 0:
+                t += float(g.exponential(1.0 / rate))
+            b["t_arrive"] = t
+        if with_state:
+            b["x"], b["v"] = uniform_fluid(box, b["n"], 1.0, int(g.integers(1 << 31)))[:2]
+        out.append(b)
+    return out
