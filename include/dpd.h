@@ -71,7 +71,11 @@ typedef struct {
                                  summed in a fixed order (bit-identical runs, about 1.5x
                                  the pair work).  Random numbers and neighbour sets are
                                  deterministic in both modes. */
-    int32_t reserved;         /* must be 0 */
+    int32_t conditional_rebuild; /* 1 (default): inside the CUDA graphs, each step's rebuild
+                                 chain sits under a conditional node that the device sets
+                                 from the rebuild flag, so steps without a rebuild launch
+                                 none of its kernels; 0: the chain is launched every step
+                                 and its kernels return at once unless flagged */
     double wait_timeout_s;    /* host wait limit per call (default 600 s) */
     void *stream;             /* cudaStream_t to run on; NULL = a stream of the handle */
 } dpd_options;

@@ -70,7 +70,10 @@ typedef struct {
 } dpd_result;
 
 /* Defaults: max_active 32, chunk_steps 100, budget 60 % of free memory,
- * dpd_default_options() for the boxes. */
+ * dpd_default_options() for the boxes with conditional_rebuild = 0 (for
+ * boxes of a few thousand particles the plain chain launches are cheaper).
+ * For more than 8 boxes to run concurrently, set CUDA_DEVICE_MAX_CONNECTIONS
+ * (e.g. to 32) in the environment before the first CUDA call. */
 void dpd_server_default_options(dpd_server_options *o);
 
 /* Start the serving loop (one host worker thread) on the current device.

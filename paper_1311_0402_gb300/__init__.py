@@ -49,7 +49,7 @@ class dpd_options(ctypes.Structure):
         ("nbr_capacity", ctypes.c_int32),
         ("graph_steps", ctypes.c_int32),
         ("deterministic", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("conditional_rebuild", ctypes.c_int32),
         ("wait_timeout_s", ctypes.c_double),
         ("stream", ctypes.c_void_p),
     ]
@@ -387,7 +387,7 @@ class Sim:
 
     def __init__(self, box, a_ij, gamma, kT, rc, s, dt, lam=0.5, skin=0.3, seed=42, body_mode=0,
                  body=(0.0, 0.0, 0.0), rebuild_every=0, nbr_capacity=0, graph_steps=8, stream=None,
-                 deterministic=0):
+                 deterministic=0, conditional_rebuild=1):
         o = dpd_default_options()
         o.skin = skin
         o.lam = lam
@@ -398,6 +398,7 @@ class Sim:
         o.nbr_capacity = nbr_capacity
         o.graph_steps = graph_steps
         o.deterministic = 1 if deterministic else 0
+        o.conditional_rebuild = 1 if conditional_rebuild else 0
         o.stream = stream
         self.box = np.asarray(box, np.float64)
         self.h = dpd_create(box, a_ij, gamma, kT, rc, s, dt, o)
@@ -473,7 +474,7 @@ class Server:
     """Continuous batching of independent boxes (include/dpd_server.h)."""
 
     def __init__(self, max_active=32, chunk_steps=100, mem_budget_bytes=0.0, skin=0.3, deterministic=0,
-                 graph_steps=8, lam=0.5):
+                 graph_steps=8, lam=0.5, conditional_rebuild=0):
         o = dpd_server_options()
         lib().dpd_server_default_options(ctypes.byref(o))
         o.max_active = max_active
@@ -483,6 +484,7 @@ class Server:
         o.box_options.deterministic = 1 if deterministic else 0
         o.box_options.graph_steps = graph_steps
         o.box_options.lam = lam
+        o.box_options.conditional_rebuild = 1 if conditional_rebuild else 0
         self.s = ctypes.c_void_p()
         _server_check(lib().dpd_server_create(ctypes.byref(o), ctypes.byref(self.s)), None)
         self._n = {}

@@ -131,10 +131,17 @@ struct Ptrs {
 // ----------------------------------------------------------------- helpers
 __host__ __device__ inline uint32_t ceil_div_u(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
 
+// The conditional-graph node guarding the next step's rebuild chain: the
+// advance kernel sets it to the rebuild flag (use = 0 outside graphs).
+struct NextCond {
+    cudaGraphConditionalHandle handle;
+    int use;
+};
+
 // launchers (each returns the launch status)
 cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s);
 // velocity-Verlet phase 1 from the full-step velocity, in place
-cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s);
+cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s, NextCond next);
 cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, int n_scan_blocks);
 // idx_of_pid for the live order (kept up to date by rebuilds only while bonds are set)
 cudaError_t launch_index(const SimParams &P, const Ptrs &D, cudaStream_t s);
@@ -146,9 +153,10 @@ cudaError_t launch_index(const SimParams &P, const Ptrs &D, cudaStream_t s);
 enum ForceMode { kForceEval = 0, kForceStep = 1, kForceFinish = 2 };
 // In Newton-3 mode the pair kernel only accumulates (fown, facc) and a
 // settle kernel completes the same mode afterwards; launch_force runs both.
-// after_pair (optional) is recorded with ev_flags right after the pair kernel.
+// after_pair (optional) is recorded with ev_flags right after the pair kernel;
+// next: the conditional node of the following step's rebuild chain.
 cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s,
-                         cudaEvent_t after_pair = nullptr, unsigned int ev_flags = 0);
+                         cudaEvent_t after_pair = nullptr, unsigned int ev_flags = 0, NextCond next = NextCond{0, 0});
 // observables: nblocks per-block partials in D.red, then their fixed-order
 // sum in D.red[nblocks * 8 .. + 8)
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s);

@@ -134,6 +134,7 @@ struct dpd_sim {
     bool has_state = false;
     bool failed = false;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;             // captures the bodies of conditional graph nodes
     bool own_stream = false;
     cudaEvent_t ev = nullptr;
     std::map<int, cudaGraphExec_t> graphs;  // steps per graph -> executable
@@ -269,36 +270,135 @@ unsigned int rec_flags(dpd_sim *h)
 
 cudaError_t rec(dpd_sim *h, cudaEvent_t e) { return cudaEventRecordWithFlags(e, h->stream, rec_flags(h)); }
 
+// Rebuild chains inside captured graphs.  Each step's chain sits in the
+// body of a conditional IF node whose handle the preceding advance kernel
+// sets from the device rebuild flag, so a step without a rebuild launches
+// none of the chain's kernels (outside graphs the chain is launched and its
+// kernels return at once when the flag is clear).  The handles default to 1
+// at every launch of the graph: an unset handle runs the chain, which still
+// checks the flag itself.
+struct CondCapture {
+    bool active = false;
+    std::vector<cudaGraphConditionalHandle> handles;  // one per step
+    std::vector<cudaGraph_t> bodies;                  // IF bodies, filled after the capture
+};
+
+cudaError_t cond_begin(dpd_sim *h, int64_t k, CondCapture &cc)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cc.handles.assign((size_t)k, 0);
+    for (int64_t s = 0; s < k && e == cudaSuccess; ++s)
+        e = cudaGraphConditionalHandleCreate(&cc.handles[(size_t)s], g, 1u, cudaGraphCondAssignDefault);
+    cc.active = e == cudaSuccess;
+    return e;
+}
+
+NextCond next_cond(const CondCapture &cc, int64_t s)
+{
+    if (!cc.active || s >= (int64_t)cc.handles.size()) return NextCond{0, 0};
+    return NextCond{cc.handles[(size_t)s], 1};
+}
+
+// The rebuild chain of step s: an IF node under capture, the chain otherwise.
+cudaError_t rebuild_step(dpd_sim *h, CondCapture &cc, int64_t s)
+{
+    if (!cc.active) return launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edata = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(h->stream, &cs, nullptr, &g, &deps, &edata, &ndeps);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = cc.handles[(size_t)s];
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, edata, ndeps, &np);
+    if (e != cudaSuccess) return e;
+    cc.bodies.push_back(np.conditional.phGraph_out[0]);
+    return cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// After the capture: each IF body gets the rebuild chain, captured on the
+// handle's side stream.
+cudaError_t cond_fill(dpd_sim *h, CondCapture &cc)
+{
+    for (cudaGraph_t body : cc.bodies) {
+        cudaError_t e = cudaStreamBeginCaptureToGraph(h->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        e = launch_rebuild(h->P, h->D, h->side, h->n_scan_blocks);
+        cudaGraph_t out = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->side, &out);
+        if (e != cudaSuccess) return e;
+        if (e2 != cudaSuccess) return e2;
+    }
+    return cudaSuccess;
+}
+
 // The kernel sequence of enqueue_steps with timing events between the
 // groups: ev[0] | phase 1 | ev[1] | rebuild | ev[2] | pair kernel | ev[3] |
 // settle + advance | ev[4] | rebuild | ev[5] ...  (3 events per step)
-cudaError_t enqueue_steps_timed(dpd_sim *h, int64_t k)
+cudaError_t enqueue_steps_timed(dpd_sim *h, int64_t k, CondCapture &cc)
 {
     cudaError_t e = rec(h, h->tev[0]);
-    if (e == cudaSuccess) e = launch_phase1(h->P, h->D, h->stream);
+    if (e == cudaSuccess) e = launch_phase1(h->P, h->D, h->stream, next_cond(cc, 0));
     if (e == cudaSuccess) e = rec(h, h->tev[1]);
     const unsigned int fl = rec_flags(h);
     for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
-        e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
+        e = rebuild_step(h, cc, s);
         if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 2]);
         if (e == cudaSuccess)
-            e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream, h->tev[3 * s + 3], fl);
+            e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream, h->tev[3 * s + 3], fl,
+                             next_cond(cc, s + 1));
         if (e == cudaSuccess) e = rec(h, h->tev[3 * s + 4]);
     }
     return e;
 }
 
 // Kernel sequence of k steps (starting and ending at a full-step state):
-// phase 1, then per step the rebuild chain (runs only when flagged) and the
-// force kernel, which integrates into the next step (or finishes the last).
-cudaError_t enqueue_steps(dpd_sim *h, int k)
+// phase 1, then per step the rebuild chain (runs only when flagged), the
+// pair kernel and the integration into the next step (or the finish of the
+// last).
+cudaError_t enqueue_steps(dpd_sim *h, int64_t k, CondCapture &cc)
 {
-    cudaError_t e = launch_phase1(h->P, h->D, h->stream);
-    for (int s = 0; s < k && e == cudaSuccess; ++s) {
-        e = launch_rebuild(h->P, h->D, h->stream, h->n_scan_blocks);
-        if (e == cudaSuccess) e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream);
+    cudaError_t e = launch_phase1(h->P, h->D, h->stream, next_cond(cc, 0));
+    for (int64_t s = 0; s < k && e == cudaSuccess; ++s) {
+        e = rebuild_step(h, cc, s);
+        if (e == cudaSuccess)
+            e = launch_force(h->P, h->D, s + 1 < k ? kForceStep : kForceFinish, false, h->stream, nullptr, 0,
+                             next_cond(cc, s + 1));
     }
     return e;
+}
+
+// Capture k steps (timed: with the events of enqueue_steps_timed) into an
+// executable graph.
+dpd_status capture_steps(dpd_sim *h, int64_t k, bool timed, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    CondCapture cc;
+    cudaError_t e = h->opt.conditional_rebuild ? cond_begin(h, k, cc) : cudaSuccess;
+    if (e == cudaSuccess) e = timed ? enqueue_steps_timed(h, k, cc) : enqueue_steps(h, k, cc);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cond_fill(h, cc);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(h, DPD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, DPD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    *out = ex;
+    return DPD_OK;
 }
 
 dpd_status get_graph(dpd_sim *h, int k, cudaGraphExec_t *out)
@@ -308,18 +408,9 @@ dpd_status get_graph(dpd_sim *h, int k, cudaGraphExec_t *out)
         *out = it->second;
         return DPD_OK;
     }
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_steps(h, k);
-    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return fail(h, DPD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
-    }
     cudaGraphExec_t ex = nullptr;
-    e = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(h, DPD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    dpd_status st = capture_steps(h, k, false, &ex);
+    if (st) return st;
     h->graphs[k] = ex;
     *out = ex;
     return DPD_OK;
@@ -466,7 +557,7 @@ void dpd_default_options(dpd_options *o)
     o->nbr_capacity = 0;
     o->graph_steps = 8;
     o->deterministic = 0;
-    o->reserved = 0;
+    o->conditional_rebuild = 1;
     o->wait_timeout_s = 600.0;
     o->stream = nullptr;
 }
@@ -561,6 +652,12 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
             return fail(nullptr, DPD_ERR_CUDA, "cudaStreamCreate failed (no GPU?)");
         }
         h->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->side = nullptr;
+        dpd_destroy(h);
+        return fail(nullptr, DPD_ERR_CUDA, "cudaStreamCreate failed");
     }
     if (cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -852,7 +949,8 @@ dpd_status dpd_step_async(dpd_sim *h, int64_t nsteps)
             left = 0;
         }
     } else {
-        CUDA_TRY(h, enqueue_steps(h, (int)left));
+        CondCapture none;
+        CUDA_TRY(h, enqueue_steps(h, left, none));
     }
     h->step += (uint64_t)nsteps;
     return DPD_OK;
@@ -915,22 +1013,14 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
         if (it != h->timed_graphs.end()) {
             ex = it->second;
         } else {
-            cudaGraph_t g = nullptr;
-            CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_steps_timed(h, nsteps);
-            cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
-            if (e != cudaSuccess || e2 != cudaSuccess) {
-                if (g) cudaGraphDestroy(g);
-                return fail(h, DPD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e ? e : e2));
-            }
-            e = cudaGraphInstantiate(&ex, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return fail(h, DPD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            st = capture_steps(h, nsteps, true, &ex);
+            if (st) return st;
             h->timed_graphs[nsteps] = ex;
         }
         CUDA_TRY(h, cudaGraphLaunch(ex, h->stream));
     } else {
-        CUDA_TRY(h, enqueue_steps_timed(h, nsteps));
+        CondCapture none;
+        CUDA_TRY(h, enqueue_steps_timed(h, nsteps, none));
     }
     h->step += (uint64_t)nsteps;
     DevCtl c;
@@ -961,9 +1051,12 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
         }
         out->steps = nsteps;
         out->force_launches = nsteps;
-        // per step: chain, force (+ settle), advance; plus the opening phase 1 + advance
-        out->kernel_launches = nsteps * (2 + kRebuildKernels + (h->P.newton3 ? 1 : 0)) + 2;
+        // per step: pair kernel (+ settle), advance; the rebuild chain on every
+        // step outside graphs, only on rebuild steps inside them (conditional
+        // nodes); plus the opening phase 1 + advance
         out->rebuilds = (int64_t)(c.nrebuild - c0.nrebuild);
+        const int64_t chains = h->opt.graph_steps > 0 && h->opt.conditional_rebuild ? out->rebuilds : nsteps;
+        out->kernel_launches = nsteps * (2 + (h->P.newton3 ? 1 : 0)) + 2 + chains * kRebuildKernels;
     }
     return DPD_OK;
 }
@@ -1105,6 +1198,7 @@ void dpd_destroy(dpd_sim *h)
     for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
     if (h->ev) cudaEventDestroy(h->ev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->side) cudaStreamDestroy(h->side);
     delete h;
 }
 

@@ -32,14 +32,17 @@ __device__ __forceinline__ void finish_block(DevCtl *ctl, bool moved)
 // One thread, after a moving kernel: the rebuild flag for the chain that
 // follows (also raised when rebuild_every steps have passed), and, when the
 // kernel integrated into the other buffer set, that set becomes the live one
-// and the step advances.
+// and the step advances.  Inside a CUDA graph the flag also sets the
+// conditional node around the next rebuild chain, so a step without a
+// rebuild launches none of the chain's kernels.
 template <bool ADVANCE, bool CHECK_EVERY>
-__global__ void k_advance(SimParams P, Ptrs D)
+__global__ void k_advance(SimParams P, Ptrs D, NextCond nc)
 {
     DevCtl *c = D.ctl;
     uint32_t next = c->rebuild_next;
     if (CHECK_EVERY && P.rebuild_every > 0 && c->since_rebuild + 1u >= (uint32_t)P.rebuild_every) next = 1u;
     c->rebuild = next;
+    if (nc.use) cudaGraphSetConditional(nc.handle, next ? 1u : 0u);
     c->rebuild_next = 0u;
     if (ADVANCE) {
         c->parity ^= 1u;
@@ -497,7 +500,7 @@ cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream
 
 template <bool ONE>
 cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, cudaStream_t s, cudaEvent_t after_pair,
-                           unsigned int ev_flags)
+                           unsigned int ev_flags, NextCond nc)
 {
     if (P.newton3) {
         // pair kernel (accumulation only), then the settle kernel of the mode
@@ -527,8 +530,8 @@ cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, 
         if (e == cudaSuccess && after_pair) e = cudaEventRecordWithFlags(after_pair, s, ev_flags);
         if (e != cudaSuccess) return e;
     }
-    if (mode == kForceStep) k_advance<true, true><<<1, 1, 0, s>>>(P, D);
-    else if (mode == kForceFinish) k_advance<true, false><<<1, 1, 0, s>>>(P, D);
+    if (mode == kForceStep) k_advance<true, true><<<1, 1, 0, s>>>(P, D, nc);
+    else if (mode == kForceFinish) k_advance<true, false><<<1, 1, 0, s>>>(P, D, nc);
     return cudaGetLastError();
 }
 
@@ -546,22 +549,22 @@ cudaError_t launch_signature(const SimParams &P, const Ptrs &D, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s)
+cudaError_t launch_phase1(const SimParams &P, const Ptrs &D, cudaStream_t s, NextCond nc)
 {
     const int g = (P.n + kThreads - 1) / kThreads;
     if (P.lambda_half)
         k_phase1<true><<<g, kThreads, 0, s>>>(P, D);
     else
         k_phase1<false><<<g, kThreads, 0, s>>>(P, D);
-    k_advance<false, true><<<1, 1, 0, s>>>(P, D);
+    k_advance<false, true><<<1, 1, 0, s>>>(P, D, nc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_fout, cudaStream_t s,
-                         cudaEvent_t after_pair, unsigned int ev_flags)
+                         cudaEvent_t after_pair, unsigned int ev_flags, NextCond nc)
 {
-    if (P.n_species == 1) return launch_force_s<true>(P, D, mode, out_fout ? 1 : 0, s, after_pair, ev_flags);
-    return launch_force_s<false>(P, D, mode, out_fout ? 1 : 0, s, after_pair, ev_flags);
+    if (P.n_species == 1) return launch_force_s<true>(P, D, mode, out_fout ? 1 : 0, s, after_pair, ev_flags, nc);
+    return launch_force_s<false>(P, D, mode, out_fout ? 1 : 0, s, after_pair, ev_flags, nc);
 }
 
 }  // namespace dpd

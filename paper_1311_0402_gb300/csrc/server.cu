@@ -261,6 +261,9 @@ void dpd_server_default_options(dpd_server_options *o)
     o->chunk_steps = 100;
     o->mem_budget_bytes = 0.0;
     dpd_default_options(&o->box_options);
+    // small boxes: launching the rebuild chain's early-exit kernels costs
+    // less than executing a conditional node's body (measured)
+    o->box_options.conditional_rebuild = 0;
 }
 
 dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out)

@@ -20,12 +20,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="fluid_large")
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--skin", type=float, default=0.3)
+    ap.add_argument("--skin", type=float, default=None)
     ap.add_argument("--box", type=float, nargs=3, default=None)
     args = ap.parse_args()
     import paper_1311_0402_gb300 as dpd
     import workloads
     dpd.lib()
+    if args.skin is None:
+        args.skin = workloads.BENCH_SKIN
     st = workloads.make(args.workload, box=args.box)
     c = st["cfg"]
     box = c["box"]

@@ -1,5 +1,5 @@
 """Parity at the full sizes of the workloads, in the configuration the
-benchmark runs (skin 0.3, CUDA graphs): every force of the 3M-particle
+benchmark runs (its skin, CUDA graphs): every force of the 3M-particle
 fluid, the 786k-bead amphiphile (3 species, harmonic bonds) and the 32k
 reverse-Poiseuille box against the FP64 oracle (1e-4 of the RMS force, max
 over all particles), sampled neighbour rows of the 3M fluid bit-exact, and
@@ -24,7 +24,7 @@ def _gpu():
 @pytest.fixture(scope="module")
 def large():
     st = workloads.make("fluid_large")
-    g, o = make_pair(st["cfg"])
+    g, o = make_pair(st["cfg"], skin=workloads.BENCH_SKIN)
     g.set_state(st["x"], st["v"], step=11)
     yield st, g, o
     g.close()
@@ -42,7 +42,7 @@ def test_fluid_large_neighbor_rows_sampled(large):
     st, g, o = large
     x32, _, _ = g.state()
     pairs = g.neighbors()
-    rl = st["cfg"]["rc"] + 0.3
+    rl = st["cfg"]["rc"] + workloads.BENCH_SKIN
     rng = np.random.default_rng(3)
     sample = rng.choice(st["n"], 128, replace=False)
     # neighbours of i from the GPU pair list (both orientations)
