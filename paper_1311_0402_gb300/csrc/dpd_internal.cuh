@@ -99,8 +99,7 @@ struct Ptrs {
     float4 *pos[2], *vel[2], *vkick[2], *force[2];
     uint32_t *tag[2], *pid[2];
     float4 *xref;             // positions at the last rebuild
-    float4 *fown;             // Newton-3 mode: each particle's own-row force sum
-    float4 *facc;             // Newton-3 mode: forces added by other particles' rows (atomics)
+    float4 *facc;             // Newton-3 mode: the force of each particle, summed by vector reductions
     float4 *fout;             // output of a standalone force evaluation
     DevCtl *ctl;
     // cells
@@ -151,7 +150,7 @@ cudaError_t launch_index(const SimParams &P, const Ptrs &D, cudaStream_t s);
 // buffer set (flips the live set, advances the step).  kForceFinish: force,
 // then phase 2 only (full-step velocity and force into the other set).
 enum ForceMode { kForceEval = 0, kForceStep = 1, kForceFinish = 2 };
-// In Newton-3 mode the pair kernel only accumulates (fown, facc) and a
+// In Newton-3 mode the pair kernel only accumulates (facc) and a
 // settle kernel completes the same mode afterwards; launch_force runs both.
 // after_pair (optional) is recorded with ev_flags right after the pair kernel;
 // next: the conditional node of the following step's rebuild chain.

@@ -460,7 +460,6 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     }
     A((void **)&D.xref, f4);
     A((void **)&D.fout, f4);
-    A((void **)&D.fown, f4);
     A((void **)&D.facc, f4);
     A((void **)&D.key, u4);
     A((void **)&D.slot, u4);

@@ -439,11 +439,11 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     float fx = w.acc[0][lane], fy = w.acc[1][lane], fz = w.acc[2][lane];
 
     if (N3) {
-        // this group's share of particle i's force; the settle kernel adds
-        // the shares other groups pushed into facc and completes the mode
+        // this group's share of particle i's force joins the shares other
+        // groups pushed into facc; the settle kernel completes the mode
         if (valid) {
             add_bonds_body(P, D, i, pi, pos, opar, fx, fy, fz);
-            D.fown[i] = make_float4(fx, fy, fz, 0.0f);
+            red_add_f4(D.facc + i, fx, fy, fz);
         }
         return;
     }
@@ -453,9 +453,10 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     if (MODE != kForceEval) finish_block(ctl, moved);
 }
 
-// Newton-3 mode: f_i = own row share + the shares other rows added, then
-// the force mode's final stage (store, or integrate into the other set).
-// Clears facc for the next evaluation.
+// Newton-3 mode: f_i = facc[i], the sum of the particle's own-group share and
+// the partner shares the pair kernel's reductions added, then the force
+// mode's final stage (store, or integrate into the other set).  Clears facc
+// for the next evaluation.
 template <int MODE, bool LHALF>
 __global__ void __launch_bounds__(kThreads) k_settle(SimParams P, Ptrs D, int out_fout)
 {
@@ -465,12 +466,10 @@ __global__ void __launch_bounds__(kThreads) k_settle(SimParams P, Ptrs D, int ou
     const unsigned long long step0 = ctl->step;
     bool moved = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const float4 a = D.fown[i];
-        const float4 b = D.facc[i];
+        const float4 f = D.facc[i];
         const float4 pi = D.pos[par][i];
         const float4 vi = D.vel[par][i];
-        moved |= integrate_particle<MODE, LHALF>(P, D, ctl, i, pi, vi, a.x + b.x, a.y + b.y, a.z + b.z, par, opar,
-                                                 step0, out_fout);
+        moved |= integrate_particle<MODE, LHALF>(P, D, ctl, i, pi, vi, f.x, f.y, f.z, par, opar, step0, out_fout);
         D.facc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (MODE != kForceEval) finish_block(ctl, moved);
