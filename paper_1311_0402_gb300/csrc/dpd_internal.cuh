@@ -159,6 +159,15 @@ cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_f
 // observables: nblocks per-block partials in D.red, then their fixed-order
 // sum in D.red[nblocks * 8 .. + 8)
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s);
+// state transfer in the caller's layout (kernels_io.cu): validation of FP64
+// x, v and species (bits into *bad), conversion into the device layout, and
+// the scatter of a float4 array to FP64 triples in caller order
+cudaError_t launch_import_check(int64_t n, int n_species, const double *x, const double *v, const int32_t *sp,
+                                uint32_t *bad, cudaStream_t s);
+cudaError_t launch_import(const SimParams &P, const double box[3], int64_t n, const double *x, const double *v,
+                          const int32_t *sp, const uint32_t *tag, float4 *pos, float4 *vel, uint32_t *tag_out,
+                          uint32_t *pid_out, cudaStream_t s);
+cudaError_t launch_export(int64_t n, const float4 *src, const uint32_t *pid, double *out, cudaStream_t s);
 cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int vel_axis, int nbins,
                            int nblocks, cudaStream_t s);
 cudaError_t launch_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *ti, const uint32_t *tj,

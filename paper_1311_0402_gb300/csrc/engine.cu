@@ -204,6 +204,32 @@ void dev_free(dpd_sim *h, void *p, std::vector<void *> &list)
     cudaFreeAsync(p, h->stream);
 }
 
+// Scratch device memory for one call, stream-ordered, freed (back to the
+// pool) when the call returns.
+struct Staging {
+    dpd_sim *h;
+    std::vector<void *> blocks;
+    cudaError_t err = cudaSuccess;
+    explicit Staging(dpd_sim *hh) : h(hh) {}
+    void *get(size_t bytes)
+    {
+        void *p = nullptr;
+        if (err == cudaSuccess) err = cudaMallocAsync(&p, bytes ? bytes : 16, h->stream);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        blocks.push_back(p);
+        return p;
+    }
+    bool ok() const { return err == cudaSuccess; }
+    std::string error() const { return cudaGetErrorString(err); }
+    ~Staging()
+    {
+        for (void *p : blocks) cudaFreeAsync(p, h->stream);
+    }
+};
+
 void free_list(dpd_sim *h, std::vector<void *> &list)
 {
     for (void *p : list) cudaFreeAsync(p, h->stream);
@@ -521,23 +547,16 @@ dpd_status guard(dpd_sim *h, bool need_state)
 // Download a float4 array and its caller indices; scatter xyz into out (n x 3).
 dpd_status download_xyz(dpd_sim *h, const float4 *dev, double *out)
 {
-    std::vector<float4> buf(h->n);
-    std::vector<uint32_t> pid(h->n);
     DevCtl c;
     dpd_status st = read_ctl(h, c);
     if (st) return st;
-    CUDA_TRY(h, cudaMemcpyAsync(buf.data(), dev, sizeof(float4) * h->n, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(pid.data(), h->D.pid[c.oparity], sizeof(uint32_t) * h->n, cudaMemcpyDeviceToHost,
-                                h->stream));
-    st = wait(h);
-    if (st) return st;
-    for (int64_t p = 0; p < h->n; ++p) {
-        uint32_t i = pid[p];
-        out[3 * (size_t)i] = buf[p].x;
-        out[3 * (size_t)i + 1] = buf[p].y;
-        out[3 * (size_t)i + 2] = buf[p].z;
-    }
-    return DPD_OK;
+    // scattered to caller order and widened on the device, one copy out
+    Staging o(h);
+    double *od = (double *)o.get(sizeof(double) * 3 * (size_t)h->n);
+    if (!o.ok()) return fail(h, DPD_ERR_OOM, "device staging for the state: " + o.error());
+    CUDA_TRY(h, launch_export(h->n, dev, h->D.pid[c.oparity], od, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(out, od, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
+    return wait(h);
 }
 
 }  // namespace
@@ -722,33 +741,34 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
     dpd_status st = guard(h, false);
     if (st) return st;
     if (n <= 0 || n > kMaxParticles || !x || !v) return fail(h, DPD_ERR_ARG, "need 0 < n <= 2^27 and x, v");
-    std::vector<float4> pos(n), vel(n);
-    std::vector<uint32_t> tg(n), pid(n);
-    for (int64_t i = 0; i < n; ++i) {
-        float xf[3];
-        for (int a = 0; a < 3; ++a) {
-            double xv = x[3 * i + a], vv = v[3 * i + a];
-            if (!std::isfinite(xv) || !std::isfinite(vv)) return fail(h, DPD_ERR_ARG, "non-finite x or v");
-            double w = xv - h->box[a] * std::floor(xv / h->box[a]);
-            float f = (float)w;
-            if (!(f < h->P.L[a])) f = 0.0f;  // rounded up to L: the same point as 0
-            if (f < 0.0f) f = 0.0f;
-            xf[a] = f;
-        }
-        int sp = species ? species[i] : 0;
-        if (sp < 0 || sp >= h->n_species) return fail(h, DPD_ERR_ARG, "species out of range");
-        float spf;
-        std::memcpy(&spf, &sp, sizeof(spf));  // species travels as int bits in pos.w
-        pos[i] = make_float4(xf[0], xf[1], xf[2], spf);
-        vel[i] = make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.0f);
-        tg[i] = tag ? tag[i] : (uint32_t)i;
-        pid[i] = (uint32_t)i;
-    }
     if (tag) {
-        std::vector<uint32_t> s(tg);
-        std::sort(s.begin(), s.end());
-        if (std::adjacent_find(s.begin(), s.end()) != s.end()) return fail(h, DPD_ERR_ARG, "tags must be distinct");
+        std::vector<uint32_t> sorted(tag, tag + n);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+            return fail(h, DPD_ERR_ARG, "tags must be distinct");
     }
+    // the caller's arrays go to device staging as they are; the checks and
+    // the conversion to the device layout run there (kernels_io.cu), and the
+    // live state is touched only once the checks pass
+    Staging in(h);
+    double *xd = (double *)in.get(sizeof(double) * 3 * (size_t)n);
+    double *vd = (double *)in.get(sizeof(double) * 3 * (size_t)n);
+    int32_t *spd = species ? (int32_t *)in.get(sizeof(int32_t) * (size_t)n) : nullptr;
+    uint32_t *tgd = tag ? (uint32_t *)in.get(sizeof(uint32_t) * (size_t)n) : nullptr;
+    uint32_t *bad = (uint32_t *)in.get(sizeof(uint32_t));
+    if (!in.ok()) return fail(h, DPD_ERR_OOM, "device staging for the state: " + in.error());
+    CUDA_TRY(h, cudaMemcpyAsync(xd, x, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(vd, v, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    if (spd) CUDA_TRY(h, cudaMemcpyAsync(spd, species, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    if (tgd) CUDA_TRY(h, cudaMemcpyAsync(tgd, tag, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(bad, 0, sizeof(uint32_t), h->stream));
+    CUDA_TRY(h, launch_import_check(n, h->n_species, xd, vd, spd, bad, h->stream));
+    uint32_t bad_h = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&bad_h, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    st = wait(h);
+    if (st) return st;
+    if (bad_h & 1u) return fail(h, DPD_ERR_ARG, "non-finite x or v");
+    if (bad_h & 2u) return fail(h, DPD_ERR_ARG, "species out of range");
     int cap = h->opt.nbr_capacity > 0 ? h->opt.nbr_capacity : auto_capacity(h, n);
     if (h->P.use_bricks) {
         // staging buffer of the brick builder: the expected halo population
@@ -774,11 +794,8 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
     h->P.has_bonds = 0;
     drop_graphs(h);
     Ptrs &D = h->D;
-    CUDA_TRY(h, cudaMemcpyAsync(D.pos[0], pos.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(D.vel[0], vel.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, launch_import(h->P, h->box, n, xd, vd, spd, tgd, D.pos[0], D.vel[0], D.tag[0], D.pid[0], h->stream));
     CUDA_TRY(h, cudaMemsetAsync(D.force[0], 0, sizeof(float4) * n, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(D.tag[0], tg.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
-    CUDA_TRY(h, cudaMemcpyAsync(D.pid[0], pid.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream));
     if (!h->P.lambda_half) CUDA_TRY(h, cudaMemsetAsync(D.vkick[0], 0, sizeof(float4) * n, h->stream));
     CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(D.facc, 0, sizeof(float4) * n, h->stream));
