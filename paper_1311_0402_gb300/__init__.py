@@ -319,10 +319,15 @@ def dpd_profile(h, bin_axis: int, vel_axis: int, nbins: int, sums=None, counts=N
     return s, c
 
 
-def dpd_get_state(h):
+def dpd_get_state(h, x=None, v=None):
+    """Positions and velocities into x, v (n x 3 float64, C order; allocated
+    when None -- pass pinned arrays to read back at full speed) and the step."""
     n = _nvec(h)
-    x = np.zeros((n, 3), np.float64)
-    v = np.zeros((n, 3), np.float64)
+    x = np.zeros((n, 3), np.float64) if x is None else x
+    v = np.zeros((n, 3), np.float64) if v is None else v
+    for a in (x, v):
+        if a.shape != (n, 3) or a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("state arrays must be C-contiguous float64 of shape (n, 3)")
     st = ctypes.c_uint64()
     _check(lib().dpd_get_state(h, _p(x, ctypes.c_double), _p(v, ctypes.c_double), ctypes.byref(st)), h)
     return x, v, st.value
@@ -456,8 +461,8 @@ class Sim:
     def profile(self, bin_axis, vel_axis, nbins, sums=None, counts=None):
         return dpd_profile(self.h, bin_axis, vel_axis, nbins, sums, counts)
 
-    def state(self):
-        return dpd_get_state(self.h)
+    def state(self, x=None, v=None):
+        return dpd_get_state(self.h, x, v)
 
     def info(self):
         return dpd_info(self.h)

@@ -35,6 +35,7 @@ constexpr int kOwnerShift = 27;                       // list entry: owner lane 
 constexpr uint32_t kIndexMask = (1u << kOwnerShift) - 1u;
 constexpr int64_t kMaxParticles = int64_t(1) << kOwnerShift;
 constexpr int kGroup = 32;                            // particles per group (one warp)
+constexpr int kForceWarps = 4;                        // groups per block of the pair kernel
 constexpr int kStencil = 27;
 // bricks: aligned kBrick^3 blocks of cells (contiguous ranges of the Morton
 // cell order) with a one-cell halo, staged in shared memory by the builder
@@ -125,6 +126,8 @@ struct Ptrs {
     const uint32_t *bond_partner;  // [n][kMaxBonds] partner caller indices
     // reductions
     double *red;                   // per-block partials
+    double *vir_part;              // [pair-kernel blocks] virial partials of the last force evaluation
+                                   // that closed a call (force evaluation or a run's last step)
 };
 
 // ----------------------------------------------------------------- helpers
@@ -177,6 +180,6 @@ int scan_blocks_for(int ncell);
 cudaError_t init_kernel_attributes();
 // largest brick_cap the builder's shared-memory limit allows
 int max_brick_cap();
-int observe_blocks_for(int ngroups);
+int observe_blocks_for(int n);
 
 }  // namespace dpd

@@ -496,7 +496,8 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     h->P.ngroups = group_count(h, n);
     A((void **)&D.gdesc, sizeof(uint2) * (size_t)h->P.ngroups);
     A((void **)&D.nbr, (size_t)h->P.ngroups * kGroup * (size_t)cap * sizeof(uint32_t));
-    h->red_doubles = std::max<size_t>((size_t)observe_blocks_for(h->P.ngroups) * 8 + 8, 4096);
+    h->red_doubles = std::max<size_t>((size_t)observe_blocks_for((int)n) * 8 + 8, 4096);
+    A((void **)&D.vir_part, sizeof(double) * (size_t)((h->P.ngroups + kForceWarps - 1) / kForceWarps));
     A((void **)&D.red, h->red_doubles * sizeof(double));
     A((void **)&D.bond_partner, sizeof(uint32_t) * (size_t)n * kMaxBonds);
     if (st) return st;
@@ -1082,7 +1083,7 @@ dpd_status dpd_observables(dpd_sim *h, dpd_obs *out)
     dpd_status st = guard(h, true);
     if (st) return st;
     if (!out) return fail(h, DPD_ERR_ARG, "out is NULL");
-    const int nb = observe_blocks_for(h->P.ngroups);
+    const int nb = observe_blocks_for((int)h->n);
     CUDA_TRY(h, launch_observe(h->P, h->D, nb, h->stream));
     double acc[8];
     CUDA_TRY(h, cudaMemcpyAsync(acc, h->D.red + (size_t)nb * 8, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));

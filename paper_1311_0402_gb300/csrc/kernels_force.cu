@@ -9,7 +9,7 @@ namespace dpd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kForceThreads = 128;
+constexpr int kForceThreads = 32 * kForceWarps;
 
 __device__ __forceinline__ float wrap_pos(float x, float L, float invL)
 {
@@ -111,9 +111,11 @@ __global__ void k_signature(SimParams P, Ptrs D)
 }
 
 // Bonds (Sec. 4.5) and the body force (Sec. 4.2) on particle i, added to f.
+// With bvir, the bonds' virial share r_ij . F_ij is added to *bvir (half per
+// end: each bond is seen from both of its particles).
 __device__ __forceinline__ void add_bonds_body(const SimParams &P, const Ptrs &D, int i, float4 pi,
                                                const float4 *__restrict__ pos, uint32_t opar, float &fx,
-                                               float &fy, float &fz)
+                                               float &fy, float &fz, float *bvir = nullptr)
 {
     if (P.has_bonds) {
         const uint32_t id = D.pid[opar][i];
@@ -134,6 +136,7 @@ __device__ __forceinline__ void add_bonds_body(const SimParams &P, const Ptrs &D
                 fx = fmaf(sc, dx, fx);
                 fy = fmaf(sc, dy, fy);
                 fz = fmaf(sc, dz, fz);
+                if (bvir) *bvir += 0.5f * (-P.k_bond * (r - P.r0_bond) * r);
             }
         }
     }
@@ -205,9 +208,9 @@ __device__ __forceinline__ bool integrate_particle(const SimParams &P, const Ptr
 template <int MODE, bool LHALF>
 __device__ __forceinline__ bool force_epilogue(const SimParams &P, const Ptrs &D, DevCtl *ctl, int i, float4 pi,
                                                float4 vi, float fx, float fy, float fz, uint32_t par, uint32_t opar,
-                                               unsigned long long step0, int out_fout)
+                                               unsigned long long step0, int out_fout, float *bvir)
 {
-    add_bonds_body(P, D, i, pi, D.pos[par], opar, fx, fy, fz);
+    add_bonds_body(P, D, i, pi, D.pos[par], opar, fx, fy, fz, bvir);
     return integrate_particle<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout);
 }
 
@@ -263,10 +266,11 @@ struct WarpSmem {
     float acc[3][32];
 };
 
-template <bool ONE_SPECIES, int SMODE, bool WRAP, bool N3>
+template <bool ONE_SPECIES, int SMODE, bool WRAP, bool N3, bool VIR>
 __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__restrict__ pos,
                                            const float4 *__restrict__ vel, const uint32_t *__restrict__ list,
-                                           uint32_t nent, int lane, WarpSmem &w, const float *a_tab, float4 *facc)
+                                           uint32_t nent, int lane, WarpSmem &w, const float *a_tab, float4 *facc,
+                                           float &vir)
 {
     const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -297,6 +301,9 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             const float xi = gauss_from_hash(A, B);
             const float a = ONE_SPECIES ? P.a[0] : a_tab[__float_as_int(w.pi[owner].w) * P.n_species + (int)(qo >> 5)];
             const float F = fmaf(a, wgt, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
+            // conservative virial r_ij . F^C_ij (each pair once in Newton-3
+            // mode, from both ends otherwise)
+            if (VIR) vir = fmaf(N3 ? 1.0f : 0.5f, a * wgt * r, vir);
             const float sc = -F * inv_r;
             fx = sc * dx;
             fy = sc * dy;
@@ -395,7 +402,26 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
     }
 }
 
-template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF, bool N3>
+// Fixed-order block sum of one value per thread into *out (thread 0).
+__device__ __forceinline__ void block_sum_double(float x, double *out)
+{
+    __shared__ double sh[kForceWarps];
+    double v = x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kForceWarps; ++k) t += sh[k];
+        *out = t;
+    }
+}
+
+// VIR: also the virial of this evaluation (conservative pairs + bonds), one
+// partial per block into D.vir_part -- for the evaluations that close a call,
+// whose positions are the state the observables describe.
+template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF, bool N3, bool VIR>
 __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, int out_fout)
 {
     constexpr int W = kForceThreads / 32;
@@ -432,24 +458,28 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     const bool all_interior = __all_sync(0xFFFFFFFFu, interior) && P.wrap_margin > 0.0f;
     __syncwarp();
     const uint32_t *__restrict__ list = D.nbr + (size_t)gid * P.gcap;
+    float vir = 0.0f;
     if (all_interior)
-        warp_pairs<ONE_SPECIES, SMODE, false, N3>(P, pos, vel, list, nent, lane, w, a_tab, D.facc);
+        warp_pairs<ONE_SPECIES, SMODE, false, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir);
     else
-        warp_pairs<ONE_SPECIES, SMODE, true, N3>(P, pos, vel, list, nent, lane, w, a_tab, D.facc);
+        warp_pairs<ONE_SPECIES, SMODE, true, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir);
     float fx = w.acc[0][lane], fy = w.acc[1][lane], fz = w.acc[2][lane];
 
     if (N3) {
         // this group's share of particle i's force joins the shares other
         // groups pushed into facc; the settle kernel completes the mode
         if (valid) {
-            add_bonds_body(P, D, i, pi, pos, opar, fx, fy, fz);
+            add_bonds_body(P, D, i, pi, pos, opar, fx, fy, fz, VIR ? &vir : nullptr);
             red_add_f4(D.facc + i, fx, fy, fz);
         }
+        if (VIR) block_sum_double(vir, D.vir_part + blockIdx.x);
         return;
     }
     bool moved = false;
     if (valid)
-        moved = force_epilogue<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout);
+        moved = force_epilogue<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout,
+                                            VIR ? &vir : nullptr);
+    if (VIR) block_sum_double(vir, D.vir_part + blockIdx.x);
     if (MODE != kForceEval) finish_block(ctl, moved);
 }
 
@@ -484,17 +514,24 @@ int grid_for(int n)
 
 constexpr int kMaxDynSmem = 160 * 1024;  // largest staging buffer the brick builder accepts
 
-template <bool ONE, int MODE, bool LH, bool N3>
-cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream_t s)
+template <bool ONE, int MODE, bool LH, bool N3, bool VIR>
+cudaError_t launch_force_v(const SimParams &P, const Ptrs &D, int of, cudaStream_t s)
 {
-    const int g = (P.ngroups + kForceThreads / 32 - 1) / (kForceThreads / 32);
+    const int g = (P.ngroups + kForceWarps - 1) / kForceWarps;
     switch (P.s_mode) {
-    case 1: k_force<ONE, 1, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
-    case 2: k_force<ONE, 2, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
-    case 3: k_force<ONE, 3, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
-    default: k_force<ONE, 0, MODE, LH, N3><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 1: k_force<ONE, 1, MODE, LH, N3, VIR><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 2: k_force<ONE, 2, MODE, LH, N3, VIR><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    case 3: k_force<ONE, 3, MODE, LH, N3, VIR><<<g, kForceThreads, 0, s>>>(P, D, of); break;
+    default: k_force<ONE, 0, MODE, LH, N3, VIR><<<g, kForceThreads, 0, s>>>(P, D, of); break;
     }
     return cudaGetLastError();
+}
+
+// The virial is taken by every evaluation except the inner steps of a run.
+template <bool ONE, int MODE, bool LH, bool N3>
+cudaError_t launch_force_m(const SimParams &P, const Ptrs &D, int of, cudaStream_t s, bool vir)
+{
+    return vir ? launch_force_v<ONE, MODE, LH, N3, true>(P, D, of, s) : launch_force_v<ONE, MODE, LH, N3, false>(P, D, of, s);
 }
 
 template <bool ONE>
@@ -503,7 +540,7 @@ cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, 
 {
     if (P.newton3) {
         // pair kernel (accumulation only), then the settle kernel of the mode
-        cudaError_t e = launch_force_m<ONE, kForceEval, true, true>(P, D, of, s);
+        cudaError_t e = launch_force_m<ONE, kForceEval, true, true>(P, D, of, s, mode != kForceStep);
         if (e == cudaSuccess && after_pair) e = cudaEventRecordWithFlags(after_pair, s, ev_flags);
         if (e != cudaSuccess) return e;
         // one thread per particle: the kernel streams memory and needs every
@@ -519,13 +556,13 @@ cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, 
         }
     } else {
         cudaError_t e;
-        if (mode == kForceEval) e = launch_force_m<ONE, kForceEval, true, false>(P, D, of, s);
+        if (mode == kForceEval) e = launch_force_m<ONE, kForceEval, true, false>(P, D, of, s, true);
         else if (P.lambda_half)
-            e = mode == kForceStep ? launch_force_m<ONE, kForceStep, true, false>(P, D, of, s)
-                                   : launch_force_m<ONE, kForceFinish, true, false>(P, D, of, s);
+            e = mode == kForceStep ? launch_force_m<ONE, kForceStep, true, false>(P, D, of, s, false)
+                                   : launch_force_m<ONE, kForceFinish, true, false>(P, D, of, s, true);
         else
-            e = mode == kForceStep ? launch_force_m<ONE, kForceStep, false, false>(P, D, of, s)
-                                   : launch_force_m<ONE, kForceFinish, false, false>(P, D, of, s);
+            e = mode == kForceStep ? launch_force_m<ONE, kForceStep, false, false>(P, D, of, s, false)
+                                   : launch_force_m<ONE, kForceFinish, false, false>(P, D, of, s, true);
         if (e == cudaSuccess && after_pair) e = cudaEventRecordWithFlags(after_pair, s, ev_flags);
         if (e != cudaSuccess) return e;
     }

@@ -31,70 +31,26 @@ __device__ void block_reduce8(double (&v)[8], double *out)
     }
 }
 
-// Observables, per-block partials of: sum v^2, sum v (3), and the virial
-// sum over pairs inside r_c of r_ij . F^C_ij plus the bonds' share (Eq. 3
-// and Sec. 4.5).  Each warp takes groups in turn: the kinetic terms of the owners, their
-// bonds (each bond seen from both ends, halved), then the group's packed
-// list 32 entries at a time -- every pair inside r_c is listed (no particle
-// has moved more than skin/2 since the build), once in Newton-3 mode and
-// from both ends otherwise, hence the pair weight.  Every sum runs in a
-// fixed order.
-template <bool ONE_SPECIES>
+// Observables, per-block partials of: sum v^2, sum v (3) over the
+// particles, and the virial sum over pairs inside r_c of r_ij . F^C_ij plus
+// the bonds' share (Eq. 3 and Sec. 4.5).  The virial comes from the force
+// evaluation that closed the last call (a force evaluation, or the last step
+// of a run): its positions are the current ones, and the pair kernel left one
+// partial per block in vir_part, summed here in a fixed order.  The kinetic
+// sums use FP64 once per particle (exact squares of the FP32 velocities).
 __global__ void __launch_bounds__(kThreads) k_observe(SimParams P, Ptrs D)
 {
-    const uint32_t par = D.ctl->parity;
-    const float4 *__restrict__ pos = D.pos[par];
-    const float4 *__restrict__ vel = D.vel[par];
-    const int lane = threadIdx.x & 31;
-    constexpr uint32_t W = kThreads / 32;
-    // FP64 arithmetic is scarce on this part: the kinetic sums (exact
-    // squares of FP32 values) use it once per particle, the pair virial is
-    // accumulated per lane in FP32 and converted once per group
+    const float4 *__restrict__ vel = D.vel[D.ctl->parity];
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const float wpair = P.newton3 ? 1.0f : 0.5f;
-    for (uint32_t gid = blockIdx.x * W + (threadIdx.x >> 5); gid < (uint32_t)P.ngroups; gid += gridDim.x * W) {
-        const uint2 desc = D.gdesc[gid];
-        const uint32_t owners = desc.y & 63u, nent = desc.y >> 6;
-        if ((uint32_t)lane < owners) {
-            const uint32_t i = desc.x + lane;
-            const float4 v = vel[i];
-            const double vx = v.x, vy = v.y, vz = v.z;
-            acc[0] += vx * vx + vy * vy + vz * vz;
-            acc[1] += vx; acc[2] += vy; acc[3] += vz;
-            if (P.has_bonds) {
-                const float4 pi = pos[i];
-                const uint32_t *bp = D.bond_partner + (size_t)D.pid[D.ctl->oparity][i] * kMaxBonds;
-                float vb = 0.0f;
-                for (int b = 0; b < kMaxBonds && bp[b] != kNone; ++b) {
-                    float4 pj = pos[D.idx_of_pid[bp[b]]];
-                    float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-                    float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-                    float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-                    float r = sqrtf(dx * dx + dy * dy + dz * dz);
-                    vb += 0.5f * (-P.k_bond * (r - P.r0_bond) * r);
-                }
-                acc[4] += (double)vb;
-            }
-        }
-        const uint32_t *__restrict__ list = D.nbr + (size_t)gid * P.gcap;
-        float vir = 0.0f;
-        for (uint32_t k = (uint32_t)lane; k < nent; k += 32u) {
-            const uint32_t e = list[k];
-            const float4 pi = pos[desc.x + (e >> kOwnerShift)];
-            const float4 pj = pos[e & kIndexMask];
-            const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
-            const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
-            const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-            const float d2 = dist2_rn(dx, dy, dz);
-            if (d2 < P.rc2 && d2 > 0.0f) {
-                const float r = sqrtf(d2);
-                const float w = fmaxf(1.0f - r * P.inv_rc, 0.0f);
-                const float a = ONE_SPECIES ? P.a[0] : P.a[__float_as_int(pi.w) * P.n_species + __float_as_int(pj.w)];
-                vir = fmaf(wpair, a * w * r, vir);
-            }
-        }
-        acc[4] += (double)vir;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += stride) {
+        const float4 v = vel[i];
+        const double vx = v.x, vy = v.y, vz = v.z;
+        acc[0] += vx * vx + vy * vy + vz * vz;
+        acc[1] += vx; acc[2] += vy; acc[3] += vz;
     }
+    const int64_t nvir = (P.ngroups + kForceWarps - 1) / kForceWarps;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvir; k += stride) acc[4] += D.vir_part[k];
     block_reduce8(acc, D.red + (size_t)blockIdx.x * 8);
 }
 
@@ -156,18 +112,15 @@ __global__ void k_pair_rng(uint64_t seed, uint32_t step, int64_t m, const uint32
 
 }  // namespace
 
-int observe_blocks_for(int ngroups)
+int observe_blocks_for(int n)
 {
-    const int g = (ngroups + kThreads / 32 - 1) / (kThreads / 32);
-    return g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g);  // grid-stride beyond 8 blocks per SM
+    const int g = (n + kThreads - 1) / kThreads;
+    return g < 1 ? 1 : (g > 152 * 4 ? 152 * 4 : g);  // grid-stride beyond 4 blocks per SM
 }
 
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s)
 {
-    if (P.n_species == 1)
-        k_observe<true><<<nblocks, kThreads, 0, s>>>(P, D);
-    else
-        k_observe<false><<<nblocks, kThreads, 0, s>>>(P, D);
+    k_observe<<<nblocks, kThreads, 0, s>>>(P, D);
     k_reduce8<<<1, kThreads, 0, s>>>(D.red, nblocks, D.red + (size_t)nblocks * 8);
     return cudaGetLastError();
 }
