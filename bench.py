@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--serve-boxes", type=int, default=512)
     ap.add_argument("--serve-active", type=int, default=32)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-conditional", action="store_true",
+                    help="launch the rebuild chain in every step's graph (for profilers that do not enter "
+                         "conditional graph nodes)")
     return ap.parse_args()
 
 
@@ -292,7 +295,8 @@ def main():
     n = st["n"]
     stream = torch.cuda.Stream()
     sim = dpd.Sim(cfg["box"], cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"], lam=cfg["lam"],
-                  skin=workloads.BENCH_SKIN, seed=workloads.TEA_SEED, stream=stream.cuda_stream)
+                  skin=workloads.BENCH_SKIN, seed=workloads.TEA_SEED, stream=stream.cuda_stream,
+                  conditional_rebuild=0 if args.no_conditional else 1)
     sim.set_state(st["x"], st["v"])
     sim.step(args.warmup)
     sampler = ClockSampler(local)

@@ -24,7 +24,8 @@ int grid_for(int64_t n)
 // to L is the same point as 0.
 __device__ __forceinline__ float wrap_to_f32(double x, double L, float Lf)
 {
-    const double w = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+    // inside the box already (the usual case): x itself, no FP64 division
+    const double w = (x >= 0.0 && x < L) ? x : __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
     float f = __double2float_rn(w);
     if (!(f < Lf)) f = 0.0f;
     if (f < 0.0f) f = 0.0f;
