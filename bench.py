@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--serve-boxes", type=int, default=512)
     ap.add_argument("--serve-active", type=int, default=32)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the skin tuner's measurement of the 3M system")
     ap.add_argument("--no-conditional", action="store_true",
                     help="launch the rebuild chain in every step's graph (for profilers that do not enter "
                          "conditional graph nodes)")
@@ -215,10 +216,28 @@ def run_serving(args):
     import workloads
     boxes = workloads.serving_stream(args.serve_boxes, with_state=True)
     total = float(sum(b["n"] * b["steps"] for b in boxes))
+    # skin per size class, chosen by the tuner on a representative box of each
+    classes = [(0, 12, 9.0), (13, 21, 17.0), (22, 1000, 26.0)]
+    tuned = {}
+    for lo, hi, L in classes:
+        probe = workloads.serving_stream(1, seed=777, L_range=(int(L), int(L)), with_state=True)[0]
+        best, table = dpd.dpd_tune_skin(probe["box"], [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, probe["x"], probe["v"],
+                                        candidates=(0.2, 0.3, 0.4, 0.5, 0.6), steps=300)
+        tuned[(lo, hi)] = (best, table)
+
+    def skin_of(b):
+        for (lo, hi), (best, _) in tuned.items():
+            if lo <= b["box"][0] <= hi:
+                return best
+        return 0.3
+
+    for b in boxes:
+        b["skin"] = skin_of(b)
     # (1) one box at a time, plain path: create, load, step, read back, free
     t0 = time.perf_counter()
     for b in boxes:
-        sim = dpd.Sim(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], seed=b["seed"])
+        sim = dpd.Sim(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], seed=b["seed"], skin=b["skin"],
+                      conditional_rebuild=0)
         sim.set_state(b["x"], b["v"])
         sim.step(b["steps"])
         sim.observables()
@@ -228,7 +247,7 @@ def run_serving(args):
 
     def submit(srv, b):
         return srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
-                          b["steps"], seed=b["seed"])
+                          b["steps"], seed=b["seed"], skin=b["skin"])
 
     # (2) saturated: everything queued at once
     srv = dpd.Server(max_active=args.serve_active, chunk_steps=100)
@@ -259,6 +278,8 @@ def run_serving(args):
         "boxes": len(boxes), "particle_steps": total, "failed": bad,
         "workload": "seeded stream of independent periodic cubes, L uniform in 6..30, rho=3 (648..81000 "
                     "particles), a in [15,40], gamma in [3,6], kT=1, dt=0.01, 500-5000 steps each",
+        "skin_by_box_length": {"L %d-%d" % (lo, min(hi, 30)): {"skin": best, "ms_per_step_tried": table}
+                               for (lo, hi), (best, table) in tuned.items()},
         "one_box_at_a_time": {"value": total / t_seq, "unit": UNIT, "wall_s": t_seq},
         "saturated": {"value": total / t_sat, "unit": UNIT, "wall_s": t_sat,
                       "vs_one_box_at_a_time": t_seq / t_sat, "max_active": args.serve_active},
@@ -294,6 +315,12 @@ def main():
     st = workloads.make(args.workload, seed=workloads.BASE_SEED + cfg["seed_offset"] + 1000 * rank)
     n = st["n"]
     stream = torch.cuda.Stream()
+    skin_table = None
+    if not args.no_tune:
+        # the tuner's measurement for this system (the run below uses the
+        # skin the full-size parity tests check)
+        _, skin_table = dpd.dpd_tune_skin(cfg["box"], cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"],
+                                          cfg["dt"], st["x"], st["v"], candidates=(0.3, 0.4, 0.5), steps=200)
     sim = dpd.Sim(cfg["box"], cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"], lam=cfg["lam"],
                   skin=workloads.BENCH_SKIN, seed=workloads.TEA_SEED, stream=stream.cuda_stream,
                   conditional_rebuild=0 if args.no_conditional else 1)
@@ -395,6 +422,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single", "l2": "working set > L2 (no flush)"},
         "phases_ms": {"integrate": integ_ms, "rebuild": rebuild_ms, "force": force_ms, "pair_kernel": pair_ms,
                       "rebuilds": rebuilds},
+        "skin_tuning_ms_per_step": skin_table,
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,

@@ -171,6 +171,23 @@ dpd_status dpd_step_async(dpd_sim *h, int64_t nsteps);
 dpd_status dpd_sync(dpd_sim *h);
 dpd_status dpd_query(dpd_sim *h, int32_t *idle);
 
+/* Choose the neighbour-list skin by measurement.  The skin trades list
+ * length (candidates per particle grow as (rc + skin)^3, Sec. 3.3) against
+ * rebuild frequency (a rebuild each time a particle has moved skin/2).  For
+ * each of the ncand candidate skins the system given by the dpd_create
+ * arguments (opt may be NULL; its skin is replaced) and the state (x, v:
+ * n x 3, species: n or NULL) runs on a temporary handle: a warm-up of
+ * steps/4 steps, then `steps` steps timed as by dpd_step_profiled.
+ * *best_skin receives the fastest candidate and ms_per_step (ncand entries,
+ * nullable) the time per step of each (infinity for a candidate that failed,
+ * e.g. a box too small for it).  Returns DPD_ERR_ARG for missing arguments,
+ * else DPD_OK if any candidate ran, else the last candidate's error.  Uses
+ * the current device; allocates and frees its own device memory. */
+dpd_status dpd_tune_skin(const double box[3], int32_t n_species, const double *a_ij, double gamma, double kT,
+                         double rc, double s, double dt, const dpd_options *opt, int64_t n, const double *x,
+                         const double *v, const int32_t *species, const double *candidates, int32_t ncand,
+                         int32_t steps, double *best_skin, double *ms_per_step);
+
 /* Per-phase device times of a run, measured with CUDA events recorded on
  * the handle's stream around every kernel group of every step. */
 typedef struct {

@@ -56,6 +56,8 @@ typedef struct {
     const double *x, *v;
     const int32_t *species;
     uint64_t steps;
+    double skin;               /* neighbour-list skin of this box; 0 = box_options.skin
+                                  (dpd_tune_skin chooses one by measurement) */
 } dpd_request;
 
 typedef struct {

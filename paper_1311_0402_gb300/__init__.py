@@ -26,7 +26,7 @@ EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds"
            "dpd_get_neighbors", "dpd_forces", "dpd_get_force", "dpd_step", "dpd_observables", "dpd_profile",
            "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled",
            "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error", "dpd_set_force",
-           "dpd_step_async", "dpd_sync", "dpd_query",
+           "dpd_step_async", "dpd_sync", "dpd_query", "dpd_tune_skin",
            # include/dpd_server.h
            "dpd_server_default_options", "dpd_server_create", "dpd_server_submit", "dpd_server_wait",
            "dpd_server_now", "dpd_server_counts", "dpd_server_last_error", "dpd_server_destroy")
@@ -92,6 +92,7 @@ class dpd_request(ctypes.Structure):
         ("v", ctypes.POINTER(ctypes.c_double)),
         ("species", ctypes.POINTER(ctypes.c_int32)),
         ("steps", ctypes.c_uint64),
+        ("skin", ctypes.c_double),
     ]
 
 
@@ -182,6 +183,8 @@ def lib():
         L.dpd_forces_static_last_error.restype = ctypes.c_char_p
         L.dpd_destroy.argtypes = [vp]
         L.dpd_destroy.restype = None
+        L.dpd_tune_skin.argtypes = [P(f64), i32, P(f64), f64, f64, f64, f64, f64, P(dpd_options), i64, P(f64),
+                                    P(f64), P(i32), P(f64), i32, i32, P(f64), P(f64)]
         L.dpd_step_async.argtypes = [vp, i64]
         L.dpd_sync.argtypes = [vp]
         L.dpd_query.argtypes = [vp, P(i32)]
@@ -283,6 +286,28 @@ def dpd_set_force(h, f):
 
 def dpd_step(h, nsteps: int):
     _check(lib().dpd_step(h, int(nsteps)), h)
+
+
+def dpd_tune_skin(box, a_ij, gamma, kT, rc, s, dt, x, v, candidates=(0.2, 0.3, 0.4, 0.5), steps=200,
+                  species=None, lam=0.5, deterministic=0):
+    """The fastest neighbour-list skin for this system, by measurement (see
+    dpd.h); returns (best_skin, {skin: ms_per_step})."""
+    a = np.ascontiguousarray(np.atleast_2d(np.asarray(a_ij, np.float64)))
+    b = np.ascontiguousarray(np.asarray(box, np.float64))
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, np.float64).reshape(-1, 3)
+    sp = None if species is None else np.ascontiguousarray(species, np.int32)
+    c = np.ascontiguousarray(np.asarray(candidates, np.float64))
+    ms = np.zeros(c.shape[0], np.float64)
+    o = dpd_default_options()
+    o.lam = lam
+    o.deterministic = 1 if deterministic else 0
+    best = ctypes.c_double()
+    _check(lib().dpd_tune_skin(_p(b, ctypes.c_double), a.shape[0], _p(a, ctypes.c_double), gamma, kT, rc, s, dt,
+                               ctypes.byref(o), x.shape[0], _p(x, ctypes.c_double), _p(v, ctypes.c_double),
+                               _p(sp, ctypes.c_int32), _p(c, ctypes.c_double), c.shape[0], int(steps),
+                               ctypes.byref(best), _p(ms, ctypes.c_double)))
+    return best.value, {float(k): float(t) for k, t in zip(c, ms)}
 
 
 def dpd_step_async(h, nsteps: int):
@@ -494,7 +519,7 @@ class Server:
         _server_check(lib().dpd_server_create(ctypes.byref(o), ctypes.byref(self.s)), None)
         self._n = {}
 
-    def submit(self, box, a_ij, gamma, kT, rc, s, dt, x, v, steps, seed=42, species=None) -> int:
+    def submit(self, box, a_ij, gamma, kT, rc, s, dt, x, v, steps, seed=42, species=None, skin=0.0) -> int:
         a = np.ascontiguousarray(np.atleast_2d(np.asarray(a_ij, np.float64)))
         x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
         v = np.ascontiguousarray(v, np.float64).reshape(-1, 3)
@@ -510,6 +535,7 @@ class Server:
         r.v = _p(v, ctypes.c_double)
         r.species = _p(sp, ctypes.c_int32) if sp is not None else None
         r.steps = int(steps)
+        r.skin = float(skin)
         t = ctypes.c_uint64()
         _server_check(lib().dpd_server_submit(self.s, ctypes.byref(r), ctypes.byref(t)), self.s)
         self._n[t.value] = x.shape[0]

@@ -39,6 +39,7 @@ struct Job {
     std::vector<double> x, v;
     std::vector<int32_t> species;
     uint64_t steps = 0;
+    double skin = 0;        // 0: the server's box_options.skin
     double est_bytes = 0;
     double t_submit = 0;
 };
@@ -63,7 +64,7 @@ struct Slot {
 double estimate_bytes(const Job &j, const dpd_options &o)
 {
     const double V = j.box[0] * j.box[1] * j.box[2];
-    const double rl = j.rc + o.skin;
+    const double rl = j.rc + (j.skin > 0.0 ? j.skin : o.skin);
     const double mean = (double)j.n / V * 4.0 / 3.0 * M_PI * rl * rl * rl;
     double cap = std::max(std::ceil(1.6 * mean + 24.0), 32.0);
     cap = std::ceil(cap / 8.0) * 8.0;
@@ -143,6 +144,7 @@ dpd_status start(dpd_server *S, Slot &sl)
 {
     dpd_options o = S->opt.box_options;
     o.seed = sl.job.seed;
+    if (sl.job.skin > 0.0) o.skin = sl.job.skin;
     o.stream = nullptr;  // a stream of the box's own
     dpd_status st = dpd_create(&sl.sim, sl.job.box, sl.job.n_species, sl.job.a.data(), sl.job.gamma, sl.job.kT,
                                sl.job.rc, sl.job.s, sl.job.dt, &o);
@@ -297,7 +299,7 @@ dpd_status dpd_server_submit(dpd_server *S, const dpd_request *r, uint64_t *tick
 {
     if (!S) return DPD_ERR_ARG;
     if (!r || !ticket || !r->a_ij || !r->x || !r->v || r->n <= 0 || r->n > dpd::kMaxParticles || r->steps < 1 ||
-        r->n_species < 1 || r->n_species > dpd::kMaxSpecies)
+        r->n_species < 1 || r->n_species > dpd::kMaxSpecies || !(r->skin >= 0.0))
         return fail_s(S, DPD_ERR_ARG, "invalid request");
     Job j;
     for (int a = 0; a < 3; ++a) j.box[a] = r->box[a];
@@ -314,6 +316,7 @@ dpd_status dpd_server_submit(dpd_server *S, const dpd_request *r, uint64_t *tick
     j.v.assign(r->v, r->v + 3 * (size_t)r->n);
     if (r->species) j.species.assign(r->species, r->species + (size_t)r->n);
     j.steps = r->steps;
+    j.skin = r->skin;
     j.est_bytes = estimate_bytes(j, S->opt.box_options);
     if (j.est_bytes > S->budget) return fail_s(S, DPD_ERR_OOM, "box needs more device memory than the budget");
     {

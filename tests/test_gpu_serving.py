@@ -127,3 +127,15 @@ def test_times_and_errors():
         srv.submit((6.0, 6.0, 6.0), [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, np.zeros((0, 3)), np.zeros((0, 3)), 10)
     assert e.value.status == 1
     srv.close()
+
+
+def test_tune_skin_picks_a_measured_candidate():
+    need_gpu()
+    st = workloads.make("fluid_small")
+    c = st["cfg"]
+    # skin 4.0 is too large for the L = 10 box (needs L > 2 (rc + skin)): refused, reported as infinity
+    best, table = dpd.dpd_tune_skin(c["box"], c["a"], c["gamma"], c["kT"], c["rc"], c["s"], c["dt"], st["x"], st["v"],
+                                    candidates=(0.2, 0.4, 4.0), steps=40)
+    assert best in (0.2, 0.4)
+    assert np.isfinite(table[0.2]) and np.isfinite(table[0.4]) and np.isinf(table[4.0])
+    assert table[best] == min(table.values())
