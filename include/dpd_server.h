@@ -35,6 +35,8 @@ typedef struct dpd_server dpd_server; /* opaque */
 
 typedef struct {
     int32_t max_active;        /* boxes resident and stepping at once (default 32) */
+    int32_t workers;           /* host worker threads sharing the boxes (default 4): creating,
+                                  loading, capturing and reading back boxes is host work */
     int32_t chunk_steps;       /* steps queued per box per scheduling pass (default 100) */
     double mem_budget_bytes;   /* device memory the boxes may take, by the server's estimate
                                   of each box; 0 (default) = 60 % of the free device memory
@@ -66,20 +68,21 @@ typedef struct {
     int64_t n;
     uint64_t steps;
     double t_submit;           /* seconds on the server clock (dpd_server_now) */
-    double t_admit;            /* admitted: device memory taken, state uploaded */
+    double t_admit;            /* admitted: taken from the queue (device memory reserved) */
     double t_done;             /* final state read back */
     dpd_obs obs;               /* observables of the final state */
 } dpd_result;
 
-/* Defaults: max_active 32, chunk_steps 100, budget 60 % of free memory,
+/* Defaults: max_active 32, 4 workers, chunk_steps 100, budget 60 % of free memory,
  * dpd_default_options() for the boxes with conditional_rebuild = 0 (for
  * boxes of a few thousand particles the plain chain launches are cheaper).
  * For more than 8 boxes to run concurrently, set CUDA_DEVICE_MAX_CONNECTIONS
  * (e.g. to 32) in the environment before the first CUDA call. */
 void dpd_server_default_options(dpd_server_options *o);
 
-/* Start the serving loop (one host worker thread) on the current device.
- * DPD_ERR_ARG for max_active < 1, chunk_steps < 1 or a negative budget. */
+/* Start the serving loop (its worker threads) on the current device.
+ * DPD_ERR_ARG for max_active < 1, workers < 1, chunk_steps < 1 or a negative
+ * budget. */
 dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out);
 
 /* Queue a box; *ticket identifies it.  The request is validated here

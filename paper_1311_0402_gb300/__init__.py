@@ -70,6 +70,7 @@ class dpd_obs(ctypes.Structure):
 class dpd_server_options(ctypes.Structure):
     _fields_ = [
         ("max_active", ctypes.c_int32),
+        ("workers", ctypes.c_int32),
         ("chunk_steps", ctypes.c_int32),
         ("mem_budget_bytes", ctypes.c_double),
         ("box_options", dpd_options),
@@ -504,10 +505,11 @@ class Server:
     """Continuous batching of independent boxes (include/dpd_server.h)."""
 
     def __init__(self, max_active=32, chunk_steps=100, mem_budget_bytes=0.0, skin=0.3, deterministic=0,
-                 graph_steps=8, lam=0.5, conditional_rebuild=0):
+                 graph_steps=8, lam=0.5, conditional_rebuild=0, workers=4):
         o = dpd_server_options()
         lib().dpd_server_default_options(ctypes.byref(o))
         o.max_active = max_active
+        o.workers = workers
         o.chunk_steps = chunk_steps
         o.mem_budget_bytes = float(mem_budget_bytes)
         o.box_options.skin = skin

@@ -42,6 +42,7 @@ struct Job {
     double skin = 0;        // 0: the server's box_options.skin
     double est_bytes = 0;
     double t_submit = 0;
+    double t_admit = 0;     // stamped under the server's lock when taken from the queue
 };
 
 struct Done {
@@ -90,7 +91,7 @@ struct dpd_server {
     double mem_used = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
-    std::thread worker;
+    std::vector<std::thread> workers;
     std::string err;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -161,7 +162,9 @@ dpd_status start(dpd_server *S, Slot &sl)
     return st;
 }
 
-void worker_loop(dpd_server *S)
+// One worker: its own set of at most `slots` running boxes; the queue, the
+// memory budget and the results are shared under the server's lock.
+void worker_loop(dpd_server *S, int slots)
 {
     cudaSetDevice(S->device);
     std::vector<Slot> active;
@@ -177,10 +180,11 @@ void worker_loop(dpd_server *S)
             if (!stopping) {
                 int looked = 0;
                 for (auto it = S->pending.begin();
-                     it != S->pending.end() && (int)(active.size() + admit.size()) < S->opt.max_active && looked < 16;) {
+                     it != S->pending.end() && (int)(active.size() + admit.size()) < slots && looked < 16;) {
                     if (S->mem_used + it->est_bytes <= S->budget) {
                         S->mem_used += it->est_bytes;
                         S->running += 1;
+                        it->t_admit = S->now();
                         admit.push_back(std::move(*it));
                         it = S->pending.erase(it);
                     } else {
@@ -196,7 +200,7 @@ void worker_loop(dpd_server *S)
             Slot &sl = active.back();
             sl.job = std::move(j);
             sl.left = sl.job.steps;
-            sl.t_admit = S->now();
+            sl.t_admit = sl.job.t_admit;
             dpd_status st = start(S, sl);
             if (st != DPD_OK) {
                 std::string msg = sl.sim ? dpd_last_error(sl.sim) : dpd_last_error(nullptr);
@@ -260,6 +264,7 @@ void dpd_server_default_options(dpd_server_options *o)
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->max_active = 32;
+    o->workers = 4;
     o->chunk_steps = 100;
     o->mem_budget_bytes = 0.0;
     dpd_default_options(&o->box_options);
@@ -274,7 +279,8 @@ dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out)
     *out = nullptr;
     dpd_server_options opt;
     if (o) opt = *o; else dpd_server_default_options(&opt);
-    if (opt.max_active < 1 || opt.chunk_steps < 1 || !(opt.mem_budget_bytes >= 0.0)) return DPD_ERR_ARG;
+    if (opt.max_active < 1 || opt.workers < 1 || opt.chunk_steps < 1 || !(opt.mem_budget_bytes >= 0.0))
+        return DPD_ERR_ARG;
     dpd_server *S = new dpd_server();
     S->opt = opt;
     S->t0 = Clock::now();
@@ -290,7 +296,11 @@ dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out)
         return DPD_ERR_CUDA;
     }
     S->budget = opt.mem_budget_bytes > 0.0 ? opt.mem_budget_bytes : 0.6 * (double)free_b;
-    S->worker = std::thread(worker_loop, S);
+    const int nw = std::min(opt.workers, opt.max_active);
+    for (int w = 0; w < nw; ++w) {
+        const int slots = opt.max_active / nw + (w < opt.max_active % nw ? 1 : 0);
+        S->workers.emplace_back(worker_loop, S, slots);
+    }
     *out = S;
     return DPD_OK;
 }
@@ -388,7 +398,8 @@ void dpd_server_destroy(dpd_server *S)
         S->stop = true;
     }
     S->cv_work.notify_all();
-    if (S->worker.joinable()) S->worker.join();
+    for (std::thread &t : S->workers)
+        if (t.joinable()) t.join();
     delete S;
 }
 
