@@ -8,7 +8,8 @@ imports nothing from it.
 The arithmetic lives in ``dpd_oracle.c`` (plain C, FP64, each routine citing
 the passage of Tang & Karniadakis, arXiv:1311.0402, that it follows); this
 module compiles it with gcc on first use and marshals numpy arrays through
-ctypes.  Everything here is argument marshalling.
+ctypes.  Everything here is argument marshalling, except the closed-form
+start-up profile of the double Poiseuille flow (Eq. 10), written out in numpy.
 
 Parity status: every routine is pinned by the ``-m "not gpu"`` tests
 (published TEA vector, Gaussian moments, hand-computed pair forces, brute
@@ -282,3 +283,28 @@ class System:
         """p = (sum m v^2 + sum_{i<j} r_ij . F_ij^{C+bond}) / (3 V)."""
         V = float(np.prod(self.box))
         return (sum_v2 + virial) / (3.0 * V)
+
+
+def double_poiseuille_startup(y, t, F, d, nu, terms=400):
+    """Eq. 10: the velocity of a fluid at rest at t = 0 driven by a body force
+    F per unit mass between planes a distance d apart (z from the midplane,
+    u = 0 at z = +-d/2):
+        u(z, t) = F d^2 / (8 nu) (1 - (2z/d)^2)
+                  - sum_n 4 (-1)^n F d^2 / (nu pi^3 (2n+1)^3) cos((2n+1) pi z / d)
+                    exp(-(2n+1)^2 pi^2 nu t / d^2),
+    with nu the kinematic viscosity, the series cut after `terms` terms.  In
+    the periodic double flow the force is +F on y in [0, d) and -F on
+    [d, 2d): each half is this profile, the second with the opposite sign;
+    y is measured along the box's 2d length."""
+    y = np.asarray(y, np.float64)
+    out = np.zeros_like(y)
+    for half, sgn in ((0, 1.0), (1, -1.0)):
+        sel = (y >= half * d) & (y < (half + 1) * d)
+        z = y[sel] - (half + 0.5) * d
+        u = F * d * d / (8.0 * nu) * (1.0 - (2.0 * z / d) ** 2)
+        for k in range(terms):
+            m = 2 * k + 1
+            u -= (4.0 * (-1) ** k * F * d * d / (nu * np.pi ** 3 * m ** 3) * np.cos(m * np.pi * z / d)
+                  * np.exp(-m * m * np.pi ** 2 * nu * t / (d * d)))
+        out[sel] = sgn * u
+    return out

@@ -142,21 +142,4 @@ __device__ __forceinline__ bool brick_stage_bulk(const Ptrs &D, uint64_t *bar, f
     return __syncthreads_and(ok);
 }
 
-// Copy the halo's particles [0, min(total, cap)) from src into dst: thread t
-// copies slots t, t + blockDim, ..., each from the cell found by binary
-// search over s_off, so every thread issues independent loads.
-__device__ __forceinline__ void brick_stage(float4 *dst, const float4 *__restrict__ src, uint32_t cap,
-                                            const uint32_t *s_off, const uint32_t *s_gstart)
-{
-    const uint32_t total = min(s_off[kHaloCells], cap);
-    for (uint32_t e = threadIdx.x; e < total; e += blockDim.x) {
-        int a = 0, bnd = kHaloCells;
-        while (bnd - a > 1) {
-            const int mid = (a + bnd) >> 1;
-            if (s_off[mid] <= e) a = mid; else bnd = mid;
-        }
-        dst[e] = src[s_gstart[a] + (e - s_off[a])];
-    }
-}
-
 }  // namespace dpd

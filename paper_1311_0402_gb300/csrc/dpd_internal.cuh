@@ -89,7 +89,7 @@ struct SimParams {
     float a[kMaxSpecies * kMaxSpecies];
     float k_bond, r0_bond;
     int has_bonds;
-    int newton3;              // half rows (j > i), each pair once, partner force by atomics
+    int newton3;              // half lists (j > i): each pair once, forces summed by vector reductions
     int use_bricks;           // every axis has >= 3 cells: the brick-staged builder
     int brick_cap;            // halo particles the brick builder stages in shared memory
     int nb[3];                // bricks per axis

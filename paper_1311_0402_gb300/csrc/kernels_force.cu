@@ -1,6 +1,8 @@
 // kernels_force.cu -- fused DPD pair force (Eqs. 2-9 with the in-situ
 // Gaussian of Sec. 3.5), harmonic bonds (Sec. 4.5), body force (Sec. 4.2),
-// and the velocity-Verlet phases (Sec. 3.1, Algorithm 1).
+// and the velocity-Verlet phases (Sec. 3.1, Algorithm 1): k_force (pairs),
+// k_settle (Newton-3 sums + integration), k_phase1, k_advance (rebuild
+// flag, buffer flip, conditional graph node).
 #include "dpd_internal.cuh"
 #include "dpd_math.cuh"
 
@@ -575,7 +577,7 @@ cudaError_t launch_force_s(const SimParams &P, const Ptrs &D, int mode, int of, 
 
 cudaError_t init_build_attributes(int max_dyn_smem);
 
-int max_brick_cap() { return kMaxDynSmem / (2 * (int)sizeof(float4)); }
+int max_brick_cap() { return kMaxDynSmem / (int)sizeof(float4); }  // staged positions only
 
 cudaError_t init_kernel_attributes() { return init_build_attributes(kMaxDynSmem); }
 

@@ -257,3 +257,24 @@ def test_equation_of_state_groot_warren():
         out[rho] = (p - rho * T) / (25.0 * rho ** 2)
     assert abs(out[8.0] - 0.101) < 0.02 * 0.101, out
     assert 0.085 < out[3.0] < out[8.0] < math.pi / 30, out
+
+
+def test_double_poiseuille_startup_closed_form():
+    """Eq. 10 as written in the oracle: zero at t = 0 (the series cancels the
+    parabola), the steady parabola F d^2 / (8 nu) (1 - (2z/d)^2) at long times,
+    the diffusion equation u_t = nu u_zz + F in between (finite differences),
+    and the opposite profile on the second half of the periodic box."""
+    F, d, nu = 0.002, 59.4, 0.27
+    y = np.linspace(0.5, 2 * d - 0.5, 400)
+    assert np.abs(oracle.double_poiseuille_startup(y, 0.0, F, d, nu)).max() < 1e-5 * F * d * d / (8 * nu)
+    z = y[y < d] - 0.5 * d
+    steady = F * d * d / (8 * nu) * (1 - (2 * z / d) ** 2)
+    late = oracle.double_poiseuille_startup(y, 1e6, F, d, nu)
+    assert np.abs(late[y < d] - steady).max() < 1e-9 * steady.max()
+    assert np.allclose(late[y >= d], -late[y < d][::-1], rtol=0, atol=1e-9 * steady.max())
+    t, dt, h = 300.0, 1e-3, 1e-2
+    yy = np.linspace(10.0, 50.0, 9)
+    u = lambda tt, yv: oracle.double_poiseuille_startup(yv, tt, F, d, nu)
+    ut = (u(t + dt, yy) - u(t - dt, yy)) / (2 * dt)
+    uzz = (u(t, yy + h) - 2 * u(t, yy) + u(t, yy - h)) / (h * h)
+    assert np.abs(ut - (nu * uzz + F)).max() < 1e-4 * F
