@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--serve-active", type=int, default=32)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the skin tuner's measurement of the 3M system")
+    ap.add_argument("--ablations", action="store_true",
+                    help="also time the atomic-insertion list builder against the ballot one (Table 2)")
     ap.add_argument("--no-conditional", action="store_true",
                     help="launch the rebuild chain in every step's graph (for profilers that do not enter "
                          "conditional graph nodes)")
@@ -289,6 +291,29 @@ def run_serving(args):
     }
 
 
+def run_list_ablation():
+    """The paper's Table 2 on this engine: the rebuild chain per rebuild with
+    the list entries placed by warp-ballot prefix sums (the default) and by one
+    atomic add per entry, for rho = 3 and 6 at 64k and 512k particles."""
+    import paper_1311_0402_gb300 as dpd
+    import workloads
+    out = []
+    for rho, n in ((3.0, 65536), (3.0, 524288), (6.0, 65536), (6.0, 524288)):
+        L = (n / rho) ** (1.0 / 3.0)
+        x, v = workloads.uniform_fluid((L, L, L), n, 1.0, 4321)
+        row = {"rho": rho, "n": n}
+        for name, lb in (("ballot", 0), ("atomic", 1)):
+            sim = dpd.Sim((L, L, L), [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, skin=0.3, list_builder=lb)
+            sim.set_state(x, v)
+            sim.step(50)
+            t = sim.step_profiled(400)
+            sim.close()
+            row[name + "_ms_per_rebuild"] = t["rebuild_ms"] / max(t["rebuilds"], 1)
+        row["atomic_over_ballot"] = row["atomic_ms_per_rebuild"] / row["ballot_ms_per_rebuild"]
+        out.append(row)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -437,6 +462,8 @@ def main():
     sim.close()
     if rank == 0 and ws == 1 and not args.no_serving:
         line["batched"] = run_serving(args)
+    if rank == 0 and ws == 1 and args.ablations:
+        line["list_builder_ablation"] = run_list_ablation()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -76,6 +76,11 @@ typedef struct {
                                  from the rebuild flag, so steps without a rebuild launch
                                  none of its kernels; 0: the chain is launched every step
                                  and its kernels return at once unless flagged */
+    int32_t list_builder;     /* 0 (default): list entries placed by warp-ballot prefix
+                                 sums (deterministic order, Sec. 3.3); 1: by an atomic add
+                                 per entry -- the paper's Table 2 comparison; the list order
+                                 (and so force summation order) then varies run to run */
+    int32_t reserved;         /* must be 0 */
     double wait_timeout_s;    /* host wait limit per call (default 600 s) */
     void *stream;             /* cudaStream_t to run on; NULL = a stream of the handle */
 } dpd_options;

@@ -50,6 +50,8 @@ class dpd_options(ctypes.Structure):
         ("graph_steps", ctypes.c_int32),
         ("deterministic", ctypes.c_int32),
         ("conditional_rebuild", ctypes.c_int32),
+        ("list_builder", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("wait_timeout_s", ctypes.c_double),
         ("stream", ctypes.c_void_p),
     ]
@@ -418,7 +420,7 @@ class Sim:
 
     def __init__(self, box, a_ij, gamma, kT, rc, s, dt, lam=0.5, skin=0.3, seed=42, body_mode=0,
                  body=(0.0, 0.0, 0.0), rebuild_every=0, nbr_capacity=0, graph_steps=8, stream=None,
-                 deterministic=0, conditional_rebuild=1):
+                 deterministic=0, conditional_rebuild=1, list_builder=0):
         o = dpd_default_options()
         o.skin = skin
         o.lam = lam
@@ -430,6 +432,7 @@ class Sim:
         o.graph_steps = graph_steps
         o.deterministic = 1 if deterministic else 0
         o.conditional_rebuild = 1 if conditional_rebuild else 0
+        o.list_builder = int(list_builder)
         o.stream = stream
         self.box = np.asarray(box, np.float64)
         self.h = dpd_create(box, a_ij, gamma, kT, rc, s, dt, o)

@@ -372,6 +372,7 @@ __device__ __forceinline__ bool within_list(const SimParams &P, float4 pj, float
 // sequence entry (cell) whose first candidate falls on lane l.
 struct CellSeq {
     uint8_t head[32];
+    uint32_t count;  // atomic-append variant: the group's running total
 };
 
 // One chunk against the owners [p_lo, p_hi) of cell slot t, kOwnersPerPass
@@ -380,46 +381,69 @@ struct CellSeq {
 // are appended in turn, so an owner's entries stay contiguous in the list.
 constexpr int kOwnersPerPass = 1;
 
-template <bool WRAP, bool STAGED, bool HALF, int NS>
+// ATOMIC (an ablation of the paper's Table 2, ballot against atomic
+// insertion): every hit takes its slot with an atomic add on the group's
+// shared counter instead of a ballot prefix; the list order then varies run
+// to run.
+template <bool WRAP, bool STAGED, bool HALF, int NS, bool ATOMIC>
 __device__ __forceinline__ uint32_t owner_pass(const SimParams &P, const float4 *__restrict__ pos,
                                                const float4 *s_pos, const uint32_t *s_off, const float4 (&cand)[kSlots],
                                                int t, uint32_t g_own, uint32_t p_lo, uint32_t p_hi, uint32_t c0,
                                                uint32_t c1, uint32_t first, uint32_t lane, uint32_t *list,
-                                               uint32_t gcap, uint32_t total)
+                                               uint32_t gcap, uint32_t total, uint32_t *count)
 {
     constexpr int NO = kOwnersPerPass;
     const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t p = p_lo; p < p_hi; p += (uint32_t)NO) {
-        uint32_t m[NO][NS];
-#pragma unroll
-        for (int o = 0; o < NO; ++o) {
-            const bool live = p + (uint32_t)o < p_hi;
-            const uint32_t po = live ? p + (uint32_t)o : p;
-            const uint32_t io = g_own + po;
-            const float4 pio = STAGED ? s_pos[s_off[t] + po] : pos[io];
-            const uint32_t k0 = HALF ? max(po + 1u, c0) : c0;
+    if constexpr (ATOMIC) {
+        for (uint32_t p = p_lo; p < p_hi; ++p) {
+            const uint32_t io = g_own + p;
+            const float4 pio = STAGED ? s_pos[s_off[t] + p] : pos[io];
+            const uint32_t k0 = HALF ? max(p + 1u, c0) : c0;
+            const uint32_t entry_owner = (io - first) << kOwnerShift;
 #pragma unroll
             for (int sl = 0; sl < NS; ++sl) {
                 const uint32_t k = c0 + 32u * sl + lane;
                 const uint32_t j = __float_as_uint(cand[sl].w);
-                m[o][sl] = __ballot_sync(0xFFFFFFFFu, live & (k < c1) & (k >= k0) & within_list<WRAP>(P, cand[sl], pio) &
-                                                          (HALF || j != io));
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < NO; ++o) {
-            const uint32_t entry_owner = (g_own + p + (uint32_t)o - first) << kOwnerShift;
-#pragma unroll
-            for (int sl = 0; sl < NS; ++sl) {
-                if ((m[o][sl] >> lane) & 1u) {
-                    const uint32_t q = total + (uint32_t)__popc(m[o][sl] & lt);
-                    if (q < gcap) list[q] = entry_owner | __float_as_uint(cand[sl].w);
+                if ((k < c1) & (k >= k0) & within_list<WRAP>(P, cand[sl], pio) & (HALF || j != io)) {
+                    const uint32_t q = atomicAdd(count, 1u);
+                    if (q < gcap) list[q] = entry_owner | j;
                 }
-                total += (uint32_t)__popc(m[o][sl]);
             }
         }
+        return total;
+    } else {
+        for (uint32_t p = p_lo; p < p_hi; p += (uint32_t)NO) {
+            uint32_t m[NO][NS];
+#pragma unroll
+            for (int o = 0; o < NO; ++o) {
+                const bool live = p + (uint32_t)o < p_hi;
+                const uint32_t po = live ? p + (uint32_t)o : p;
+                const uint32_t io = g_own + po;
+                const float4 pio = STAGED ? s_pos[s_off[t] + po] : pos[io];
+                const uint32_t k0 = HALF ? max(po + 1u, c0) : c0;
+#pragma unroll
+                for (int sl = 0; sl < NS; ++sl) {
+                    const uint32_t k = c0 + 32u * sl + lane;
+                    const uint32_t j = __float_as_uint(cand[sl].w);
+                    m[o][sl] = __ballot_sync(0xFFFFFFFFu, live & (k < c1) & (k >= k0) & within_list<WRAP>(P, cand[sl], pio) &
+                                                              (HALF || j != io));
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < NO; ++o) {
+                const uint32_t entry_owner = (g_own + p + (uint32_t)o - first) << kOwnerShift;
+#pragma unroll
+                for (int sl = 0; sl < NS; ++sl) {
+                    if ((m[o][sl] >> lane) & 1u) {
+                        const uint32_t q = total + (uint32_t)__popc(m[o][sl] & lt);
+                        if (q < gcap) list[q] = entry_owner | __float_as_uint(cand[sl].w);
+                    }
+                    total += (uint32_t)__popc(m[o][sl]);
+                }
+            }
+        }
+        return total;
     }
-    return total;
 }
 
 // The owners [p_lo, p_hi) (places in cell slot t) of a group whose first
@@ -427,7 +451,7 @@ __device__ __forceinline__ uint32_t owner_pass(const SimParams &P, const float4 
 // the group list; returns the new running total.  A chunk of kChunk
 // candidates is held in registers, lane l holding entries c0 + 32 s + l;
 // every owner of the cell tests against the same registers (owner_pass).
-template <bool WRAP, bool STAGED, bool HALF>
+template <bool WRAP, bool STAGED, bool HALF, bool ATOMIC>
 __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 *__restrict__ pos,
                                                const float4 *s_pos, const uint32_t *s_off, const uint32_t *s_gstart,
                                                const uint32_t *s_cnt, CellSeq &w, int t, uint32_t p_lo, uint32_t p_hi,
@@ -492,17 +516,18 @@ __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 
         }
         const uint32_t ns = (c1 - c0 + 31u) / 32u;  // live slots of this chunk
         if (ns == 4u)
-            total = owner_pass<WRAP, STAGED, HALF, 4>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
+            total = owner_pass<WRAP, STAGED, HALF, 4, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
         else if (ns == 3u)
-            total = owner_pass<WRAP, STAGED, HALF, 3>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
+            total = owner_pass<WRAP, STAGED, HALF, 3, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
         else if (ns == 2u)
-            total = owner_pass<WRAP, STAGED, HALF, 2>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
+            total = owner_pass<WRAP, STAGED, HALF, 2, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
         else
-            total = owner_pass<WRAP, STAGED, HALF, 1>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total);
+            total = owner_pass<WRAP, STAGED, HALF, 1, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
     }
     return total;
 }
 
+template <bool ATOMIC>
 __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
@@ -552,6 +577,10 @@ __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, 
         }
         uint32_t *list = D.nbr + (size_t)(gbase + q) * gcap;
         uint32_t total = 0;
+        if (ATOMIC) {
+            if (lane == 0) w.count = 0u;
+            __syncwarp();
+        }
         // the group's particles are sorted by cell: take the cells in turn
         for (uint32_t l0 = 0; l0 < owners;) {
             const int t = __shfl_sync(0xFFFFFFFFu, t_lane, (int)l0);
@@ -562,20 +591,24 @@ __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, 
             const uint32_t p_hi = p_lo + run;
             if (P.newton3) {
                 if (!local)
-                    total = build_cell<true, false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                    total = build_cell<true, false, true, ATOMIC>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
                 else if (inner)
-                    total = build_cell<false, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                    total = build_cell<false, true, true, ATOMIC>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
                 else
-                    total = build_cell<true, true, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                    total = build_cell<true, true, true, ATOMIC>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
             } else {
                 if (!local)
-                    total = build_cell<true, false, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                    total = build_cell<true, false, false, ATOMIC>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
                 else if (inner)
-                    total = build_cell<false, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                    total = build_cell<false, true, false, ATOMIC>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
                 else
-                    total = build_cell<true, true, false>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
+                    total = build_cell<true, true, false, ATOMIC>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
             }
             l0 += run;
+        }
+        if (ATOMIC) {
+            __syncwarp();
+            total = w.count;
         }
         if (lane == 0) write_group(D, P, gbase + q, first, owners, total);
         local_max = total > local_max ? total : local_max;
@@ -591,7 +624,9 @@ int scan_blocks_for(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 
 cudaError_t init_build_attributes(int max_dyn_smem)
 {
-    return cudaFuncSetAttribute(k_nbuild_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    cudaError_t e = cudaFuncSetAttribute(k_nbuild_brick<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_nbuild_brick<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
 }
 
 cudaError_t launch_index(const SimParams &P, const Ptrs &D, cudaStream_t s)
@@ -616,7 +651,11 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
         k_gather<false><<<gg, kThreads, 0, s>>>(P, D);
     k_commit<<<1, 1, 0, s>>>(D);
     if (P.use_bricks) {
-        k_nbuild_brick<<<P.nbricks, kBuildThreads, sizeof(float4) * (size_t)P.brick_cap, s>>>(P, D);
+        const size_t smem = sizeof(float4) * (size_t)P.brick_cap;
+        if (P.list_builder == 1)
+            k_nbuild_brick<true><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
+        else
+            k_nbuild_brick<false><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
     } else {
         k_nbuild<<<g, kThreads, 0, s>>>(P, D);
     }

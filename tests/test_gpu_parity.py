@@ -171,3 +171,18 @@ def test_step_counter_and_rebuilds_progress():
     assert g.info()["rebuilds"] > r0
     ob = g.observables()
     assert abs(ob["momentum"]).max() < 1e-2
+
+
+def test_atomic_insertion_builder_same_pairs():
+    """The atomic-insertion list builder (the paper's Table 2 comparison)
+    lists the same pairs as the oracle, in another order, and gives the same
+    forces."""
+    st = workloads.make("fluid_small")
+    cfg = st["cfg"]
+    g, o = make_pair(cfg, list_builder=1)
+    g.set_state(st["x"], st["v"], step=3)
+    x32, v32, _ = g.state()
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, cfg["box"], cfg["rc"] + 0.3))
+    fo, _ = o.forces(x32, v32, step=3)
+    err, rms = force_error(g.forces(), fo)
+    assert err < FORCE_TOL, (err, rms)
