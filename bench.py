@@ -314,6 +314,28 @@ def run_list_ablation():
     return out
 
 
+def run_reorder_ablation():
+    """The paper's reorder on/off comparison (Sec. 3.2) on the 3M fluid: the
+    whole step with the particles reordered into cell order at every rebuild
+    (the default) and kept in their load order (uniformly random in space)."""
+    import paper_1311_0402_gb300 as dpd
+    import workloads
+    st = workloads.make("fluid_large")
+    c = st["cfg"]
+    out = {"workload": "fluid_large (3M, load order uniformly random in space), skin %g" % workloads.BENCH_SKIN}
+    for name, nr in (("reordered", 0), ("load_order", 1)):
+        sim = dpd.Sim(c["box"], c["a"], c["gamma"], c["kT"], c["rc"], c["s"], c["dt"], skin=workloads.BENCH_SKIN,
+                      no_reorder=nr)
+        sim.set_state(st["x"], st["v"])
+        sim.step(20)
+        t = sim.step_profiled(200)
+        sim.close()
+        out[name] = {"ms_per_step": t["total_ms"] / 200, "pair_ms": t["pair_ms"] / 200,
+                     "rebuild_ms_per_rebuild": t["rebuild_ms"] / max(t["rebuilds"], 1)}
+    out["speedup_from_reordering"] = out["load_order"]["ms_per_step"] / out["reordered"]["ms_per_step"]
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -464,6 +486,7 @@ def main():
         line["batched"] = run_serving(args)
     if rank == 0 and ws == 1 and args.ablations:
         line["list_builder_ablation"] = run_list_ablation()
+        line["reorder_ablation"] = run_reorder_ablation()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

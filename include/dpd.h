@@ -80,7 +80,10 @@ typedef struct {
                                  sums (deterministic order, Sec. 3.3); 1: by an atomic add
                                  per entry -- the paper's Table 2 comparison; the list order
                                  (and so force summation order) then varies run to run */
-    int32_t reserved;         /* must be 0 */
+    int32_t no_reorder;       /* 0 (default): at every rebuild the particles are reordered
+                                 into cell order (Sec. 3.2); 1: they stay in load order and
+                                 the list is built through the sort permutation -- the
+                                 paper's reorder on/off comparison (Sec. 3.2); slower */
     double wait_timeout_s;    /* host wait limit per call (default 600 s) */
     void *stream;             /* cudaStream_t to run on; NULL = a stream of the handle */
 } dpd_options;

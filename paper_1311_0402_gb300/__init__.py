@@ -51,7 +51,7 @@ class dpd_options(ctypes.Structure):
         ("deterministic", ctypes.c_int32),
         ("conditional_rebuild", ctypes.c_int32),
         ("list_builder", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("no_reorder", ctypes.c_int32),
         ("wait_timeout_s", ctypes.c_double),
         ("stream", ctypes.c_void_p),
     ]
@@ -420,7 +420,7 @@ class Sim:
 
     def __init__(self, box, a_ij, gamma, kT, rc, s, dt, lam=0.5, skin=0.3, seed=42, body_mode=0,
                  body=(0.0, 0.0, 0.0), rebuild_every=0, nbr_capacity=0, graph_steps=8, stream=None,
-                 deterministic=0, conditional_rebuild=1, list_builder=0):
+                 deterministic=0, conditional_rebuild=1, list_builder=0, no_reorder=0):
         o = dpd_default_options()
         o.skin = skin
         o.lam = lam
@@ -433,6 +433,7 @@ class Sim:
         o.deterministic = 1 if deterministic else 0
         o.conditional_rebuild = 1 if conditional_rebuild else 0
         o.list_builder = int(list_builder)
+        o.no_reorder = 1 if no_reorder else 0
         o.stream = stream
         self.box = np.asarray(box, np.float64)
         self.h = dpd_create(box, a_ij, gamma, kT, rc, s, dt, o)

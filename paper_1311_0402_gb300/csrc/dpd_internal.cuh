@@ -92,6 +92,7 @@ struct SimParams {
     int newton3;              // half lists (j > i): each pair once, forces summed by vector reductions
     int use_bricks;           // every axis has >= 3 cells: the brick-staged builder
     int list_builder;         // 0: ballot insertion; 1: atomic insertion (ablation)
+    int no_reorder;           // 1: particles stay in load order (ablation; tile builder, no bricks)
     int brick_cap;            // halo particles the brick builder stages in shared memory
     int nb[3];                // bricks per axis
     int nbricks;

@@ -578,7 +578,7 @@ void dpd_default_options(dpd_options *o)
     o->deterministic = 0;
     o->conditional_rebuild = 1;
     o->list_builder = 0;
-    o->reserved = 0;
+    o->no_reorder = 0;
     o->wait_timeout_s = 600.0;
     o->stream = nullptr;
 }
@@ -604,6 +604,7 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
         }
     if (o.body_force_mode < 0 || o.body_force_mode > 2) return fail(nullptr, DPD_ERR_ARG, "body_force_mode in 0..2");
     if (o.list_builder < 0 || o.list_builder > 1) return fail(nullptr, DPD_ERR_ARG, "list_builder in 0..1");
+    if (o.no_reorder < 0 || o.no_reorder > 1) return fail(nullptr, DPD_ERR_ARG, "no_reorder in 0..1");
     if (o.rebuild_every < 0 || o.graph_steps < 0 || o.nbr_capacity < 0 || !(o.wait_timeout_s > 0))
         return fail(nullptr, DPD_ERR_ARG, "rebuild_every, graph_steps, nbr_capacity >= 0; wait_timeout_s > 0");
     const double rl = rc + o.skin;
@@ -689,7 +690,8 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     keep_pool_memory();
     build_geometry(nc, h->geo);
     h->n_scan_blocks = scan_blocks_for(P.ncell);
-    P.use_bricks = (nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3) ? 1 : 0;
+    P.no_reorder = o.no_reorder;
+    P.use_bricks = (!o.no_reorder && nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3) ? 1 : 0;
     P.list_builder = o.list_builder;
     for (int a = 0; a < 3; ++a) P.nb[a] = h->geo.nb[a];
     P.nbricks = h->geo.nb[0] * h->geo.nb[1] * h->geo.nb[2];

@@ -37,18 +37,46 @@ __device__ void block_reduce8(double (&v)[8], double *out)
 // evaluation that closed the last call (a force evaluation, or the last step
 // of a run): its positions are the current ones, and the pair kernel left one
 // partial per block in vir_part, summed here in a fixed order.  The kinetic
-// sums use FP64 once per particle (exact squares of the FP32 velocities).
+// sums are exact to about 2^-48 per thread (Sum2), then FP64.
+// Error-free FP32 accumulation (FP64 arithmetic is scarce on this part):
+// s + c carries the exact running sum of a few dozen terms to about 2^-48
+// relative (Knuth's TwoSum for each addition; a square enters as its exact
+// two-term split hi + lo, hi = v v rounded, lo = fma(v, v, -hi)).
+struct Sum2 {
+    float s = 0.0f, c = 0.0f;
+    // every operation rounded on its own: a contracted multiply-add would
+    // break the error-free transformations
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        s = t;
+    }
+    __device__ __forceinline__ void add_square(float v)
+    {
+        const float hi = __fmul_rn(v, v);
+        add(hi);
+        c = __fadd_rn(c, fmaf(v, v, -hi));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __global__ void __launch_bounds__(kThreads) k_observe(SimParams P, Ptrs D)
 {
     const float4 *__restrict__ vel = D.vel[D.ctl->parity];
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Sum2 v2, px, py, pz;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += stride) {
         const float4 v = vel[i];
-        const double vx = v.x, vy = v.y, vz = v.z;
-        acc[0] += vx * vx + vy * vy + vz * vz;
-        acc[1] += vx; acc[2] += vy; acc[3] += vz;
+        v2.add_square(v.x);
+        v2.add_square(v.y);
+        v2.add_square(v.z);
+        px.add(v.x);
+        py.add(v.y);
+        pz.add(v.z);
     }
+    double acc[8] = {v2.value(), px.value(), py.value(), pz.value(), 0, 0, 0, 0};
     const int64_t nvir = (P.ngroups + kForceWarps - 1) / kForceWarps;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nvir; k += stride) acc[4] += D.vir_part[k];
     block_reduce8(acc, D.red + (size_t)blockIdx.x * 8);

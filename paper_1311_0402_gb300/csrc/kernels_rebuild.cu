@@ -195,7 +195,9 @@ __global__ void k_rank(SimParams P, Ptrs D)
     }
 }
 
-template <bool LHALF>
+// IDENT (reorder ablation): the arrays keep their order; the copy into the
+// other buffer set is the identity.
+template <bool LHALF, bool IDENT>
 __global__ void k_gather(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
@@ -204,7 +206,7 @@ __global__ void k_gather(SimParams P, Ptrs D)
     const int lim = P.n > P.ncell ? P.n : P.ncell;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lim; p += gridDim.x * blockDim.x) {
         if (p < P.n) {
-            uint32_t i = D.perm[p];
+            uint32_t i = IDENT ? (uint32_t)p : D.perm[p];
             float4 x = D.pos[s][i];
             D.pos[t][p] = x;
             D.xref[p] = x;
@@ -273,7 +275,10 @@ __device__ __forceinline__ void write_group(const Ptrs &D, const SimParams &P, u
 
 // Builder for grids with fewer than three cells along some axis (no
 // bricks): groups are the 32-aligned tiles, candidates come from the
-// deduplicated cell stencil in global memory.
+// deduplicated cell stencil in global memory.  NOREORDER (reorder ablation):
+// the particles stay in load order, so a cell's members are found through
+// the sort permutation and the half-list rule is tested per candidate.
+template <bool NOREORDER>
 __global__ void k_nbuild(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
@@ -297,7 +302,7 @@ __global__ void k_nbuild(SimParams P, Ptrs D)
                 }
                 b = D.cell_start[cc];
                 n = D.cell_start[cc + 1] - b;
-                e = (P.newton3 && i >= b) ? i + 1u - b : 0u;
+                e = (!NOREORDER && P.newton3 && i >= b) ? i + 1u - b : 0u;
             }
         };
         next_cell();
@@ -309,12 +314,12 @@ __global__ void k_nbuild(SimParams P, Ptrs D)
             bool hit = false;
             uint32_t j = 0;
             if (act) {
-                j = b + e;
+                j = NOREORDER ? D.perm[b + e] : b + e;
                 const float4 pj = pos[j];
                 const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
                 const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
                 const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
-                hit = (dist2_rn(dx, dy, dz) < P.rlist2) & (P.newton3 || j != i);
+                hit = (dist2_rn(dx, dy, dz) < P.rlist2) & (P.newton3 ? (!NOREORDER || j > i) : j != i);
                 ++e;
                 if (e >= n) next_cell();
             }
@@ -645,10 +650,13 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
     k_scatter<<<g, kThreads, 0, s>>>(P, D);
     k_rank<<<g, kThreads, 0, s>>>(P, D);
     const int gg = grid_for(P.n > P.ncell ? P.n : P.ncell);
-    if (P.lambda_half)
-        k_gather<true><<<gg, kThreads, 0, s>>>(P, D);
-    else
-        k_gather<false><<<gg, kThreads, 0, s>>>(P, D);
+    if (P.no_reorder) {
+        if (P.lambda_half) k_gather<true, true><<<gg, kThreads, 0, s>>>(P, D);
+        else k_gather<false, true><<<gg, kThreads, 0, s>>>(P, D);
+    } else {
+        if (P.lambda_half) k_gather<true, false><<<gg, kThreads, 0, s>>>(P, D);
+        else k_gather<false, false><<<gg, kThreads, 0, s>>>(P, D);
+    }
     k_commit<<<1, 1, 0, s>>>(D);
     if (P.use_bricks) {
         const size_t smem = sizeof(float4) * (size_t)P.brick_cap;
@@ -656,8 +664,10 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
             k_nbuild_brick<true><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
         else
             k_nbuild_brick<false><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
+    } else if (P.no_reorder) {
+        k_nbuild<true><<<g, kThreads, 0, s>>>(P, D);
     } else {
-        k_nbuild<<<g, kThreads, 0, s>>>(P, D);
+        k_nbuild<false><<<g, kThreads, 0, s>>>(P, D);
     }
     return cudaGetLastError();
 }

@@ -186,3 +186,24 @@ def test_atomic_insertion_builder_same_pairs():
     fo, _ = o.forces(x32, v32, step=3)
     err, rms = force_error(g.forces(), fo)
     assert err < FORCE_TOL, (err, rms)
+
+
+@pytest.mark.parametrize("deterministic", [0, 1])
+def test_no_reorder_ablation_same_physics(deterministic):
+    """With the particles kept in load order (the paper's reorder on/off
+    comparison) the list and the forces are the same, also after steps that
+    rebuild the list."""
+    st = workloads.make("fluid_small")
+    cfg = st["cfg"]
+    g, o = make_pair(cfg, no_reorder=1, deterministic=deterministic)
+    g.set_state(st["x"], st["v"], step=3)
+    x32, v32, step = g.state()
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, cfg["box"], cfg["rc"] + 0.3))
+    fo, _ = o.forces(x32, v32, step=step)
+    assert force_error(g.forces(), fo)[0] < FORCE_TOL
+    g.step(25)
+    assert g.info()["rebuilds"] > 1
+    x32, v32, step = g.state()
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, cfg["box"], cfg["rc"] + 0.3))
+    fo, _ = o.forces(x32, v32, step=step)
+    assert force_error(g.forces(), fo)[0] < FORCE_TOL
