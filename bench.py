@@ -131,6 +131,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sel)}
 
 
+def slowest(pg, local, device):
+    """The largest of every rank's `local` (the job's wall time is its
+    slowest rank's); `local` itself without a process group."""
+    if not pg:
+        return float(local)
+    import torch
+    t = torch.tensor([float(local)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, per_rank_units, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank has the same work)."""
+    return ws * per_rank_units / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -404,12 +421,8 @@ def main():
     rebuilds = sum(t["rebuilds"] for t in times)
     integ_ms = sum(t["integrate_ms"] for t in times)
     rebuild_ms = sum(t["rebuild_ms"] for t in times)
-    max_ms = total_ms
-    if pg:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        max_ms = float(tt.item())
-    value = ws * n * args.steps / (max_ms / 1e3)
+    max_ms = slowest(pg, total_ms, "cuda")
+    value = job_rate(ws, n * args.steps, max_ms / 1e3)
 
     # roofline of the dominant kernel (the fused pair force)
     rho = n / float(np.prod(cfg["box"]))
@@ -445,14 +458,10 @@ def main():
         sim.observables()
     sim.state(xo, vo)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = slowest(pg, time.perf_counter() - t0, "cuda")
     state_bytes = n * 6 * 8
     obs_bytes = 8 * 8 + 48  # the eight device-reduced sums + the control word
-    e2e = {"value": ws * n * e2e_steps / e2e_s, "unit": UNIT,
+    e2e = {"value": job_rate(ws, n * e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(state_bytes / e2e_steps),
            "d2h_bytes_per_step": int(state_bytes / e2e_steps + obs_bytes),
            "steps": e2e_steps,
