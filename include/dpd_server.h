@@ -106,6 +106,8 @@ double dpd_server_now(const dpd_server *s);
 dpd_status dpd_server_counts(dpd_server *s, int64_t *queued, int64_t *running, int64_t *finished,
                              double *mem_bytes);
 
+/* The last failure message (a submit, a wait or a box's run); the string
+ * belongs to the calling thread and stays valid until its next call. */
 const char *dpd_server_last_error(const dpd_server *s);
 
 /* Stop the loop: queued boxes are dropped, running boxes are stopped after

@@ -387,7 +387,14 @@ dpd_status dpd_server_counts(dpd_server *S, int64_t *queued, int64_t *running, i
 const char *dpd_server_last_error(const dpd_server *S)
 {
     if (!S) return "null server";
-    return S->err.c_str();
+    // workers may set the message at any time: hand out a copy owned by the
+    // calling thread (valid until its next call)
+    thread_local std::string copy;
+    {
+        std::lock_guard<std::mutex> lk(const_cast<dpd_server *>(S)->m);
+        copy = S->err;
+    }
+    return copy.c_str();
 }
 
 void dpd_server_destroy(dpd_server *S)
