@@ -196,6 +196,15 @@ dpd_status dpd_tune_skin(const double box[3], int32_t n_species, const double *a
                          const double *v, const int32_t *species, const double *candidates, int32_t ncand,
                          int32_t steps, double *best_skin, double *ms_per_step);
 
+/* Failure-detection self-test: runs the device's bounded wait (the one the
+ * neighbour builder uses for its TMA-staged halos) on a transaction that
+ * nothing delivers.  The wait gives up after `polls` polls (1..2^20), sets
+ * the timeout bit of the device error word, and the call returns
+ * DPD_ERR_TIMEOUT -- the status a real stalled copy produces.  The bit is
+ * cleared afterwards; the handle and its state stay usable.  Needs a loaded
+ * state (DPD_ERR_STATE otherwise). */
+dpd_status dpd_wait_selftest(dpd_sim *h, uint32_t polls);
+
 /* Per-phase device times of a run, measured with CUDA events recorded on
  * the handle's stream around every kernel group of every step. */
 typedef struct {

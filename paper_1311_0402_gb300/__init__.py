@@ -26,7 +26,7 @@ EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds"
            "dpd_get_neighbors", "dpd_forces", "dpd_get_force", "dpd_step", "dpd_observables", "dpd_profile",
            "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled",
            "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error", "dpd_set_force",
-           "dpd_step_async", "dpd_sync", "dpd_query", "dpd_tune_skin",
+           "dpd_step_async", "dpd_sync", "dpd_query", "dpd_tune_skin", "dpd_wait_selftest",
            # include/dpd_server.h
            "dpd_server_default_options", "dpd_server_create", "dpd_server_submit", "dpd_server_wait",
            "dpd_server_now", "dpd_server_counts", "dpd_server_last_error", "dpd_server_destroy")
@@ -189,6 +189,7 @@ def lib():
         L.dpd_tune_skin.argtypes = [P(f64), i32, P(f64), f64, f64, f64, f64, f64, P(dpd_options), i64, P(f64),
                                     P(f64), P(i32), P(f64), i32, i32, P(f64), P(f64)]
         L.dpd_step_async.argtypes = [vp, i64]
+        L.dpd_wait_selftest.argtypes = [vp, u32]
         L.dpd_sync.argtypes = [vp]
         L.dpd_query.argtypes = [vp, P(i32)]
         L.dpd_server_default_options.argtypes = [P(dpd_server_options)]
@@ -311,6 +312,12 @@ def dpd_tune_skin(box, a_ij, gamma, kT, rc, s, dt, x, v, candidates=(0.2, 0.3, 0
                                _p(sp, ctypes.c_int32), _p(c, ctypes.c_double), c.shape[0], int(steps),
                                ctypes.byref(best), _p(ms, ctypes.c_double)))
     return best.value, {float(k): float(t) for k, t in zip(c, ms)}
+
+
+def dpd_wait_selftest(h, polls: int = 1024) -> int:
+    """Status of the device's bounded-wait self-test (DPD_ERR_TIMEOUT = 6
+    when the wait gave up as it should)."""
+    return int(lib().dpd_wait_selftest(h, int(polls)))
 
 
 def dpd_step_async(h, nsteps: int):

@@ -178,6 +178,8 @@ cudaError_t launch_profile(const SimParams &P, const Ptrs &D, int bin_axis, int 
 cudaError_t launch_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t *ti, const uint32_t *tj,
                             uint32_t *out_hash, float *out_xi, cudaStream_t s);
 int scan_blocks_for(int ncell);
+// the bounded device wait on a transaction that never arrives (failure-detection probe)
+cudaError_t launch_wait_probe(const Ptrs &D, uint32_t polls, cudaStream_t s);
 // one-time kernel attributes (dynamic shared memory of the brick kernels)
 cudaError_t init_kernel_attributes();
 // largest brick_cap the builder's shared-memory limit allows

@@ -1007,6 +1007,22 @@ dpd_status dpd_query(dpd_sim *h, int32_t *idle)
     return fail(h, DPD_ERR_CUDA, std::string("kernel failure: ") + cudaGetErrorString(e));
 }
 
+dpd_status dpd_wait_selftest(dpd_sim *h, uint32_t polls)
+{
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (polls < 1 || polls > (1u << 20)) return fail(h, DPD_ERR_ARG, "polls must be in 1..2^20");
+    if (h->pending && (st = dpd_sync(h)) != DPD_OK) return st;
+    CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+    CUDA_TRY(h, launch_wait_probe(h->D, polls, h->stream));
+    DevCtl c;
+    st = check_err(h, c);
+    // the probe's error bit must not leak into the next call
+    CUDA_TRY(h, cudaMemsetAsync(&h->D.ctl->err, 0, sizeof(uint32_t), h->stream));
+    dpd_status st2 = wait(h);
+    return st != DPD_OK ? st : st2;
+}
+
 dpd_status dpd_step(dpd_sim *h, int64_t nsteps)
 {
     dpd_status st = dpd_step_async(h, nsteps);

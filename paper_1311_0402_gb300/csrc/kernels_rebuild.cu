@@ -623,7 +623,29 @@ __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, 
     if (lane == 0 && local_max) atomicMax(&D.ctl->max_nnb, local_max);
 }
 
+// Failure-detection probe: the bounded mbarrier wait of the brick staging,
+// on a transaction that nothing delivers (expect_tx with no copy issued).
+// The wait gives up after `polls` polls and the timeout bit is set; no
+// asynchronous copy is in flight, so the block exits cleanly.
+__global__ void k_wait_probe(Ptrs D, uint32_t polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_arrive_expect_tx(&bar, 16u);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u, polls);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(&D.ctl->err, kErrTimeout);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(const Ptrs &D, uint32_t polls, cudaStream_t s)
+{
+    k_wait_probe<<<1, 32, 0, s>>>(D, polls);
+    return cudaGetLastError();
+}
 
 int scan_blocks_for(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 

@@ -129,3 +129,44 @@ def test_newton3_and_deterministic_modes_agree():
     a.step(5)
     b.step(5)
     assert np.abs(a.state()[0] - b.state()[0]).max() < 1e-5
+
+
+def test_launch_modes_give_identical_trajectories():
+    """The same step sequence launched three ways -- captured graphs with the
+    rebuild chain under conditional nodes, captured graphs launching the chain
+    every step, and eager launches without graphs -- gives bit-identical
+    states and the same rebuilds (deterministic mode: fixed summation order).
+    Each dpd_step call is one velocity-Verlet unit, so the eager run steps in
+    the graphs' 8-step units."""
+    st = workloads.make("fluid_small")
+    c = st["cfg"]
+    outs = []
+    for graph_steps, cond, calls in ((8, 1, [48]), (8, 0, [48]), (0, 1, [8] * 6)):
+        g = dpd.Sim(c["box"], c["a"], c["gamma"], c["kT"], c["rc"], c["s"], c["dt"], graph_steps=graph_steps,
+                    conditional_rebuild=cond, deterministic=1)
+        g.set_state(st["x"], st["v"])
+        for k in calls:
+            g.step(k)
+        x, v, step = g.state()
+        outs.append((x, v, step, g.info()["rebuilds"]))
+        g.close()
+    for x, v, step, rebuilds in outs[1:]:
+        assert step == outs[0][2] == 48
+        assert rebuilds == outs[0][3] and rebuilds > 2
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(v, outs[0][1])
+
+
+def test_bounded_device_wait_reports_timeout_and_recovers():
+    """Failure detection without a fault: the device's bounded wait (the one
+    guarding the builder's TMA-staged halos) on a transaction that nothing
+    delivers gives up, the host reads DPD_ERR_TIMEOUT, and the handle keeps
+    working."""
+    st = workloads.make("fluid_small")
+    c = st["cfg"]
+    g, o = make_pair(c)
+    g.set_state(st["x"], st["v"])
+    assert dpd.dpd_wait_selftest(g.h, 256) == 6  # DPD_ERR_TIMEOUT
+    g.step(10)
+    x32, v32, step = g.state()
+    fo, _ = o.forces(x32, v32, step=step)
+    assert force_error(g.forces(), fo)[0] < 1e-4
