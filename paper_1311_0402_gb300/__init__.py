@@ -29,7 +29,12 @@ EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds"
            "dpd_step_async", "dpd_sync", "dpd_query", "dpd_tune_skin", "dpd_wait_selftest",
            # include/dpd_server.h
            "dpd_server_default_options", "dpd_server_create", "dpd_server_submit", "dpd_server_wait",
-           "dpd_server_now", "dpd_server_counts", "dpd_server_last_error", "dpd_server_destroy")
+           "dpd_server_now", "dpd_server_counts", "dpd_server_last_error", "dpd_server_destroy",
+           # include/dpd_ensemble.h
+           "dpd_ensemble_default_options", "dpd_ensemble_create", "dpd_ensemble_fits", "dpd_ensemble_add",
+           "dpd_ensemble_remove", "dpd_ensemble_step", "dpd_ensemble_sync", "dpd_ensemble_get_state",
+           "dpd_ensemble_get_forces", "dpd_ensemble_observables", "dpd_ensemble_info", "dpd_ensemble_tune",
+           "dpd_ensemble_config", "dpd_ensemble_destroy", "dpd_ensemble_last_error")
 
 
 class DPDError(RuntimeError):
@@ -142,6 +147,32 @@ class dpd_static_params(ctypes.Structure):
     ]
 
 
+class dpd_ensemble_options(ctypes.Structure):
+    _fields_ = [
+        ("threads", ctypes.c_int32),
+        ("cluster", ctypes.c_int32),
+        ("wait_timeout_s", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class dpd_box_params(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double * 3),
+        ("n_species", ctypes.c_int32),
+        ("a_ij", ctypes.POINTER(ctypes.c_double)),
+        ("gamma", ctypes.c_double),
+        ("kT", ctypes.c_double),
+        ("rc", ctypes.c_double),
+        ("s", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("lam", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("body_force_mode", ctypes.c_int32),
+        ("body_force", ctypes.c_double * 3),
+    ]
+
+
 _lib = None
 
 
@@ -204,6 +235,24 @@ def lib():
         L.dpd_server_last_error.restype = ctypes.c_char_p
         L.dpd_server_destroy.argtypes = [vp]
         L.dpd_server_destroy.restype = None
+        L.dpd_ensemble_default_options.argtypes = [P(dpd_ensemble_options)]
+        L.dpd_ensemble_default_options.restype = None
+        L.dpd_ensemble_create.argtypes = [P(vp), P(dpd_ensemble_options)]
+        L.dpd_ensemble_fits.argtypes = [P(dpd_box_params), i64]
+        L.dpd_ensemble_add.argtypes = [vp, P(dpd_box_params), i64, P(f64), P(f64), P(i32), u64, P(i32)]
+        L.dpd_ensemble_remove.argtypes = [vp, i32]
+        L.dpd_ensemble_step.argtypes = [vp, P(i32), P(i32), i32]
+        L.dpd_ensemble_sync.argtypes = [vp]
+        L.dpd_ensemble_get_state.argtypes = [vp, i32, P(f64), P(f64), P(u64)]
+        L.dpd_ensemble_get_forces.argtypes = [vp, i32, P(f64)]
+        L.dpd_ensemble_observables.argtypes = [vp, i32, P(dpd_obs)]
+        L.dpd_ensemble_info.argtypes = [vp, P(i32), P(i64)]
+        L.dpd_ensemble_tune.argtypes = [vp, i32, P(f64)]
+        L.dpd_ensemble_config.argtypes = [vp, P(i32), P(i32)]
+        L.dpd_ensemble_destroy.argtypes = [vp]
+        L.dpd_ensemble_destroy.restype = None
+        L.dpd_ensemble_last_error.argtypes = [vp]
+        L.dpd_ensemble_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -585,6 +634,136 @@ class Server:
         if self.s is not None and self.s.value:
             lib().dpd_server_destroy(self.s)
         self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ ensemble kernel
+def _ens_check(st, e):
+    if st != DPD_OK:
+        m = lib().dpd_ensemble_last_error(e)
+        raise DPDError(st, m.decode() if m else "")
+
+
+def dpd_box_params_from(box, a_ij, gamma, kT, rc, s, dt, lam=0.5, seed=42, body_mode=0, body=(0.0, 0.0, 0.0)):
+    """dpd_box_params and the a_ij array it points to (keep both alive)."""
+    a = np.ascontiguousarray(np.atleast_2d(np.asarray(a_ij, np.float64)))
+    p = dpd_box_params()
+    p.box[:] = [float(b) for b in box]
+    p.n_species = a.shape[0]
+    p.a_ij = _p(a, ctypes.c_double)
+    p.gamma, p.kT, p.rc, p.s, p.dt, p.lam = gamma, kT, rc, s, dt, lam
+    p.seed = seed
+    p.body_force_mode = body_mode
+    p.body_force[:] = [float(b) for b in body]
+    return p, a
+
+
+def dpd_ensemble_fits(box, a_ij, gamma, kT, rc, s, dt, n, lam=0.5) -> bool:
+    p, _a = dpd_box_params_from(box, a_ij, gamma, kT, rc, s, dt, lam)
+    return bool(lib().dpd_ensemble_fits(ctypes.byref(p), int(n)))
+
+
+class Ensemble:
+    """Many small boxes advanced together by the ensemble kernel
+    (include/dpd_ensemble.h): one thread-block cluster per box, the box
+    resident in shared memory for a whole chunk of steps."""
+
+    def __init__(self, threads=0, cluster=0, wait_timeout_s=600.0):
+        o = dpd_ensemble_options()
+        lib().dpd_ensemble_default_options(ctypes.byref(o))
+        o.threads, o.cluster, o.wait_timeout_s = threads, cluster, wait_timeout_s
+        self.e = ctypes.c_void_p()
+        _ens_check(lib().dpd_ensemble_create(ctypes.byref(self.e), ctypes.byref(o)), None)
+        self._n = {}
+
+    def add(self, box, a_ij, gamma, kT, rc, s, dt, x, v, species=None, step=0, lam=0.5, seed=42, body_mode=0,
+            body=(0.0, 0.0, 0.0)) -> int:
+        p, _a = dpd_box_params_from(box, a_ij, gamma, kT, rc, s, dt, lam, seed, body_mode, body)
+        x = np.ascontiguousarray(x, np.float64).reshape(-1, 3)
+        v = np.ascontiguousarray(v, np.float64).reshape(-1, 3)
+        if v.shape != x.shape:
+            raise ValueError("x and v must have the same shape")
+        sp = None if species is None else np.ascontiguousarray(species, np.int32)
+        i = ctypes.c_int32()
+        _ens_check(lib().dpd_ensemble_add(self.e, ctypes.byref(p), x.shape[0], _p(x, ctypes.c_double),
+                                          _p(v, ctypes.c_double), _p(sp, ctypes.c_int32), int(step), ctypes.byref(i)),
+                   self.e)
+        self._n[i.value] = x.shape[0]
+        return i.value
+
+    def remove(self, box_id):
+        _ens_check(lib().dpd_ensemble_remove(self.e, int(box_id)), self.e)
+        self._n.pop(box_id, None)
+
+    def step(self, steps, ids=None):
+        """Advance boxes ids (all when None) by steps (an int, or one per id);
+        asynchronous, see sync()."""
+        if ids is None:
+            st = np.array([int(steps)], np.int32)
+            _ens_check(lib().dpd_ensemble_step(self.e, None, _p(st, ctypes.c_int32), 0), self.e)
+            return
+        ids = np.ascontiguousarray(ids, np.int32).reshape(-1)
+        st = np.ascontiguousarray(np.broadcast_to(np.asarray(steps, np.int32), ids.shape), np.int32)
+        _ens_check(lib().dpd_ensemble_step(self.e, _p(ids, ctypes.c_int32), _p(st, ctypes.c_int32), ids.size),
+                   self.e)
+
+    def sync(self):
+        _ens_check(lib().dpd_ensemble_sync(self.e), self.e)
+
+    def _count(self, box_id):
+        n = self._n.get(box_id)
+        if n is None:
+            raise DPDError(1, "unknown box id %r" % (box_id,))
+        return n
+
+    def state(self, box_id):
+        n = self._count(box_id)
+        x = np.zeros((n, 3), np.float64)
+        v = np.zeros((n, 3), np.float64)
+        step = ctypes.c_uint64()
+        _ens_check(lib().dpd_ensemble_get_state(self.e, int(box_id), _p(x, ctypes.c_double), _p(v, ctypes.c_double),
+                                                ctypes.byref(step)), self.e)
+        return x, v, step.value
+
+    def forces(self, box_id):
+        f = np.zeros((self._count(box_id), 3), np.float64)
+        _ens_check(lib().dpd_ensemble_get_forces(self.e, int(box_id), _p(f, ctypes.c_double)), self.e)
+        return f
+
+    def observables(self, box_id):
+        o = dpd_obs()
+        _ens_check(lib().dpd_ensemble_observables(self.e, int(box_id), ctypes.byref(o)), self.e)
+        return dict(step=o.step, n=o.n, kinetic=o.kinetic, temperature=o.temperature, virial=o.virial,
+                    pressure=o.pressure, momentum=np.array(list(o.momentum)))
+
+    def info(self):
+        nb, npart = ctypes.c_int32(), ctypes.c_int64()
+        _ens_check(lib().dpd_ensemble_info(self.e, ctypes.byref(nb), ctypes.byref(npart)), self.e)
+        return nb.value, npart.value
+
+    def tune(self, steps=50):
+        """Autotune threads per CTA and CTAs per box for each size class
+        present; returns the last class's table {(threads, cluster): ms per step}."""
+        t = np.zeros(12, np.float64)
+        _ens_check(lib().dpd_ensemble_tune(self.e, int(steps), _p(t, ctypes.c_double)), self.e)
+        return {(T, C): float(t[ti * 4 + ci]) for ti, T in enumerate((128, 256, 512))
+                for ci, C in enumerate((1, 2, 4, 8))}
+
+    def config(self):
+        th = np.zeros(4, np.int32)
+        cl = np.zeros(4, np.int32)
+        _ens_check(lib().dpd_ensemble_config(self.e, _p(th, ctypes.c_int32), _p(cl, ctypes.c_int32)), self.e)
+        return th.tolist(), cl.tolist()
+
+    def close(self):
+        if self.e is not None and self.e.value:
+            lib().dpd_ensemble_destroy(self.e)
+        self.e = None
 
     def __del__(self):
         try:

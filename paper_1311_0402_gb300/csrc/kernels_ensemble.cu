@@ -1,0 +1,569 @@
+// kernels_ensemble.cu -- the ensemble kernel: many small boxes, each owned by
+// a thread-block cluster, advanced a whole chunk of steps per launch with the
+// box resident in shared memory.
+//
+// Every CTA of a box's cluster holds a replica of the box (positions, the
+// velocity the pair force reads with the particle's signature, the
+// half-kicked velocity when lambda != 1/2) and, each step:
+//   1. bins the box into cells of side >= r_c (Sec. 3.3.1): a counting sort
+//      by shared-memory atomics, then each cell's members put in index order,
+//      so every replica holds the same cell lists;
+//   2. evaluates the pair forces of its share of the cells: work units of
+//      consecutive cells go round-robin to the cluster's CTAs and their warps.
+//      A warp takes a unit cell by cell; the 27-cell stencil of a cell is
+//      gathered once (with each neighbour cell's periodic shift) and every
+//      owner of the cell tests it 32 candidates at a time.  Hits inside r_c
+//      (the FP32 predicate of the other kernels) go to a per-warp ring in
+//      shared memory, evaluated 32 pairs at a time by the whole warp (Eqs.
+//      2-9, the TEA hash and Box-Muller Gaussian of Sec. 3.5), and summed per
+//      owner by a segmented shuffle scan (each pair is seen from both sides).
+//      Within a candidate round every owner's hits are one run of the ring;
+//      the ring is emptied between rounds, so a batch never holds two runs of
+//      one owner;
+//   3. integrates the particles of its cells (the lambda form of velocity
+//      Verlet, Sec. 3.1 / Algorithm 1) and stores their new state into every
+//      replica of the cluster through distributed shared memory.
+// Two cluster barriers per step separate the reads of a step from the
+// writes of the next.  The last step writes positions, full-step velocities
+// and forces (w = the particle's virial share) to device memory.
+//
+// Fixed summation order: units never span a queue flush, a cell's members are
+// in index order and the stencil order is fixed, so a force does not depend on
+// the cluster size, the block size or the other boxes of the launch.
+#include "dpd_math.cuh"
+#include "ensemble.cuh"
+
+#include <algorithm>
+#include <cooperative_groups.h>
+#include <mutex>
+
+namespace cg = cooperative_groups;
+
+namespace dpd {
+
+namespace {
+
+constexpr int kEnsMaxThreads = 512;
+constexpr int kObsThreads = 256;
+
+// x wrapped into [0, L) (the same arithmetic as the other integrators).
+__device__ __forceinline__ float ens_wrap(float x, float L, float invL)
+{
+    x = x - L * floorf(x * invL);
+    if (x >= L) x -= L;
+    if (x < 0.0f) x += L;
+    if (x >= L) x = 0.0f;
+    return x;
+}
+
+__device__ __forceinline__ int ens_axis(float x, float cpl, int nc)
+{
+    const int c = (int)(x * cpl);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__device__ __forceinline__ int ens_cell(const EnsBox &B, float4 p)
+{
+    return (ens_axis(p.z, B.cpl[2], B.nc[2]) * B.nc[1] + ens_axis(p.y, B.cpl[1], B.nc[1])) * B.nc[0] +
+           ens_axis(p.x, B.cpl[0], B.nc[0]);
+}
+
+// periodic shift of a neighbour cell along one axis: 0 none, 1 +L, 2 -L
+__device__ __forceinline__ float ens_shift(uint32_t code, float L)
+{
+    return code == 1u ? L : (code == 2u ? -L : 0.0f);
+}
+
+struct EnsPtrs {
+    float4 *pos, *u, *vh, *f;
+    uint32_t *start, *cnt;
+    uint16_t *idx, *slot;
+};
+
+// Exclusive scan of cnt[0, ncell) into start[0, ncell], start[ncell] = total.
+__device__ void ens_scan(const uint32_t *cnt, uint32_t *start, int ncell, uint32_t *wsum)
+{
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = T >> 5;
+    const int per = (ncell + T - 1) / T;
+    const int lo = min(ncell, t * per), hi = min(ncell, lo + per);
+    uint32_t sum = 0;
+    for (int c = lo; c < hi; ++c) sum += cnt[c];
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < nw ? wsum[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) wsum[lane] = wi - w;
+        if (lane == 31) wsum[32] = wi;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + incl - sum;
+    for (int c = lo; c < hi; ++c) {
+        start[c] = run;
+        run += cnt[c];
+    }
+    if (t == 0) start[ncell] = wsum[32];
+    __syncthreads();
+}
+
+// Evaluate ring entries [head, head + nb) (nb <= 32), one pair per lane, and
+// add the sums of each run of equal owners to the owner's accumulator.
+template <int SMODE, bool VIR>
+__device__ __forceinline__ void ens_batch(const EnsBox &B, const EnsPtrs &S, const float4 *q, const uint32_t (&key)[4],
+                                          uint32_t head, int nb, int lane)
+{
+    __syncwarp();
+    float fx = 0.f, fy = 0.f, fz = 0.f, fw = 0.f;
+    uint32_t owner = 0x10000u + (uint32_t)lane;  // distinct dummy owners for idle lanes
+    if (lane < nb) {
+        const float4 e = q[(head + (uint32_t)lane) & (kEnsQueue - 1)];
+        const uint32_t pk = __float_as_uint(e.w);
+        const uint32_t i = pk >> 16, j = pk & 0xFFFFu;
+        owner = i;
+        const float4 wi = S.u[i], vj = S.u[j];
+        const float dx = e.x, dy = e.y, dz = e.z;
+        const float d2 = dist2_rn(dx, dy, dz);
+        const float inv_r = rsqrtf(d2);
+        const float r = d2 * inv_r;
+        const float wgt = fmaxf(fmaf(-r, B.inv_rc, 1.0f), 0.0f);
+        const float wR = weight_R<SMODE>(wgt, B.s);
+        // e_ij = -d / r; e . v_ij = -(d . (v_i - v_j)) / r
+        const float ev = -((dx * (wi.x - vj.x) + dy * (wi.y - vj.y)) + dz * (wi.z - vj.z)) * inv_r;
+        uint32_t A, Bw;
+        pair_hash(__float_as_uint(wi.w), __float_as_uint(vj.w), key, A, Bw);
+        const float xi = gauss_from_hash(A, Bw);
+        float a = B.a[0];
+        if (B.n_species > 1) a = B.a[__float_as_int(S.pos[i].w) * B.n_species + __float_as_int(S.pos[j].w)];
+        const float F = fmaf(a, wgt, fmaf(-B.gamma * wR * wR, ev, B.sigma_isdt * wR * xi));
+        if (VIR) fw = 0.5f * (a * wgt * r);  // each pair is seen from both ends
+        const float sc = -F * inv_r;
+        fx = sc * dx;
+        fy = sc * dy;
+        fz = sc * dz;
+    }
+    // segmented inclusive scan over runs of equal owners (fixed order)
+    const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, owner, 1);
+    const uint32_t heads = __ballot_sync(0xFFFFFFFFu, lane == 0 || prev != owner);
+    const int first = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float ax = __shfl_up_sync(0xFFFFFFFFu, fx, d);
+        const float ay = __shfl_up_sync(0xFFFFFFFFu, fy, d);
+        const float az = __shfl_up_sync(0xFFFFFFFFu, fz, d);
+        float aw = 0.f;
+        if (VIR) aw = __shfl_up_sync(0xFFFFFFFFu, fw, d);
+        if (lane - first >= d) {
+            fx += ax;
+            fy += ay;
+            fz += az;
+            if (VIR) fw += aw;
+        }
+    }
+    const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, owner, 1);
+    if (lane < nb && (lane == 31 || next != owner)) {
+        float4 acc = S.f[owner];
+        acc.x += fx;
+        acc.y += fy;
+        acc.z += fz;
+        if (VIR) acc.w += fw;
+        S.f[owner] = acc;
+    }
+    __syncwarp();
+}
+
+// Pair forces of the owners in work unit u (cells [u K, u K + K)) into S.f.
+template <int SMODE, bool VIR>
+__device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t *cand, int u, int lane)
+{
+    const uint32_t key[4] = {B.key[0], B.key[1], B.key[2], B.key[3]};
+    const uint32_t lt = (1u << lane) - 1u;
+    const int c0 = u * kEnsUnitCells, c1 = min(c0 + kEnsUnitCells, B.ncell);
+    const int ncx = B.nc[0], ncy = B.nc[1], ncz = B.nc[2];
+    uint32_t head = 0u, tail = 0u;
+    for (int c = c0; c < c1; ++c) {
+        const int ob = (int)S.start[c], oe = (int)S.start[c + 1];
+        if (ob == oe) continue;
+        for (int k = ob + lane; k < oe; k += 32) S.f[S.idx[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
+        // lane l < 27: neighbour cell l of the stencil, its member range and shift
+        const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+        int len = 0, sbeg = 0;
+        uint32_t code = 0u;
+        if (lane < 27) {
+            int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+            uint32_t kx = 0u, ky = 0u, kz = 0u;
+            if (x < 0) { x += ncx; kx = 2u; } else if (x >= ncx) { x -= ncx; kx = 1u; }
+            if (y < 0) { y += ncy; ky = 2u; } else if (y >= ncy) { y -= ncy; ky = 1u; }
+            if (z < 0) { z += ncz; kz = 2u; } else if (z >= ncz) { z -= ncz; kz = 1u; }
+            const int cc = (z * ncy + y) * ncx + x;
+            sbeg = (int)S.start[cc];
+            len = (int)S.start[cc + 1] - sbeg;
+            code = kx | (ky << 2) | (kz << 4);
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int pre = incl - len;
+        const int ncand = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        for (int base = 0; base < ncand; base += kEnsCand) {
+            __syncwarp();
+            if (lane < 27) {
+                const int lo = max(pre, base), hi = min(pre + len, base + kEnsCand);
+                for (int p = lo; p < hi; ++p) cand[p - base] = (uint32_t)S.idx[sbeg + p - pre] | (code << 16);
+            }
+            __syncwarp();
+            const int nch = min(kEnsCand, ncand - base);
+            for (int o = ob; o < oe; ++o) {
+                const uint32_t i = S.idx[o];
+                const float4 pi = S.pos[i];
+                for (int t0 = 0; t0 < nch; t0 += 32) {
+                    const int t = t0 + lane;
+                    bool hit = false;
+                    float dx = 0.f, dy = 0.f, dz = 0.f;
+                    uint32_t j = 0u;
+                    if (t < nch) {
+                        const uint32_t e = cand[t];
+                        j = e & 0xFFFFu;
+                        const float4 pj = S.pos[j];
+                        dx = __fadd_rn(__fsub_rn(pj.x, pi.x), ens_shift((e >> 16) & 3u, B.L[0]));
+                        dy = __fadd_rn(__fsub_rn(pj.y, pi.y), ens_shift((e >> 18) & 3u, B.L[1]));
+                        dz = __fadd_rn(__fsub_rn(pj.z, pi.z), ens_shift((e >> 20) & 3u, B.L[2]));
+                        const float d2 = dist2_rn(dx, dy, dz);
+                        hit = (d2 < B.rc2) & (d2 > 0.0f);
+                    }
+                    const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+                    if (hit)
+                        q[(tail + __popc(m & lt)) & (kEnsQueue - 1)] =
+                            make_float4(dx, dy, dz, __uint_as_float((i << 16) | j));
+                    tail += (uint32_t)__popc(m);
+                    if (tail - head >= 32u) {
+                        ens_batch<SMODE, VIR>(B, S, q, key, head, 32, lane);
+                        head += 32u;
+                    }
+                }
+            }
+            // another round visits the same owners again: empty the ring first,
+            // so no batch holds two runs of one owner (their adds would race)
+            if (base + kEnsCand < ncand) {
+                while (tail != head) {
+                    const int nb = (int)min(32u, tail - head);
+                    ens_batch<SMODE, VIR>(B, S, q, key, head, nb, lane);
+                    head += (uint32_t)nb;
+                }
+            }
+        }
+    }
+    while (tail != head) {
+        const int nb = (int)min(32u, tail - head);
+        ens_batch<SMODE, VIR>(B, S, q, key, head, nb, lane);
+        head += (uint32_t)nb;
+    }
+}
+
+template <bool LHALF, int SMODE>
+__global__ void __launch_bounds__(kEnsMaxThreads, 1) k_ens_run(const EnsBox *__restrict__ boxes, int C)
+{
+    __shared__ EnsBox B;
+    __shared__ uint32_t wsum[33];
+    extern __shared__ __align__(16) unsigned char smem[];
+
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(boxes + blockIdx.x / C);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&B);
+        for (int k = threadIdx.x; k < (int)(sizeof(EnsBox) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = C > 1 ? (int)cl.block_rank() : 0;
+    const int n = B.n, ncell = B.ncell, T = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = T >> 5;
+    const EnsLayout lay = ens_layout(n, ncell, LHALF, T);
+    EnsPtrs S;
+    S.pos = reinterpret_cast<float4 *>(smem + lay.pos);
+    S.u = reinterpret_cast<float4 *>(smem + lay.u);
+    S.vh = reinterpret_cast<float4 *>(smem + lay.vh);
+    S.f = reinterpret_cast<float4 *>(smem + lay.f);
+    S.start = reinterpret_cast<uint32_t *>(smem + lay.start);
+    S.cnt = reinterpret_cast<uint32_t *>(smem + lay.cnt);
+    S.idx = reinterpret_cast<uint16_t *>(smem + lay.idx);
+    S.slot = reinterpret_cast<uint16_t *>(smem + lay.slot);
+    float4 *q = reinterpret_cast<float4 *>(smem + lay.q) + warp * kEnsQueue;
+    uint32_t *cand = reinterpret_cast<uint32_t *>(smem + lay.cand) + warp * kEnsCand;
+    const int steps = B.steps;
+    const unsigned long long step0 = B.step;
+    const float invL[3] = {1.0f / B.L[0], 1.0f / B.L[1], 1.0f / B.L[2]};
+
+    // replica of the box; with steps > 0, phase 1 of the first step:
+    //   u = v + dt/2 f,  x += dt u,  v~ = v + lambda dt f (= u when lambda = 1/2)
+    for (int i = threadIdx.x; i < n; i += T) {
+        float4 x = B.pos[i];
+        const float4 v = B.vel[i];
+        const uint32_t tg = __ldg(B.tag + i);
+        if (steps == 0) {
+            S.pos[i] = x;
+            S.u[i] = make_float4(v.x, v.y, v.z, __uint_as_float(signature(tg, (uint32_t)step0, B.key)));
+        } else {
+            const float4 f = B.frc[i];
+            const float ux = fmaf(B.half_dt, f.x, v.x), uy = fmaf(B.half_dt, f.y, v.y), uz = fmaf(B.half_dt, f.z, v.z);
+            x.x = ens_wrap(fmaf(B.dt, ux, x.x), B.L[0], invL[0]);
+            x.y = ens_wrap(fmaf(B.dt, uy, x.y), B.L[1], invL[1]);
+            x.z = ens_wrap(fmaf(B.dt, uz, x.z), B.L[2], invL[2]);
+            S.pos[i] = x;
+            const float sig = __uint_as_float(signature(tg, (uint32_t)(step0 + 1ull), B.key));
+            if (LHALF) {
+                S.u[i] = make_float4(ux, uy, uz, sig);
+            } else {
+                S.u[i] = make_float4(fmaf(B.lambda_dt, f.x, v.x), fmaf(B.lambda_dt, f.y, v.y),
+                                     fmaf(B.lambda_dt, f.z, v.z), sig);
+                S.vh[i] = make_float4(ux, uy, uz, 0.0f);
+            }
+        }
+    }
+    for (int c = threadIdx.x; c < ncell; c += T) S.cnt[c] = 0u;
+    __syncthreads();
+
+    const int nunits = (ncell + kEnsUnitCells - 1) / kEnsUnitCells;
+    const int nforce = steps == 0 ? 1 : steps;
+    for (int s = 1; s <= nforce; ++s) {
+        const bool last = s == nforce;
+        // 1. cell lists
+        for (int i = threadIdx.x; i < n; i += T) S.slot[i] = (uint16_t)atomicAdd(&S.cnt[ens_cell(B, S.pos[i])], 1u);
+        __syncthreads();
+        ens_scan(S.cnt, S.start, ncell, wsum);
+        for (int i = threadIdx.x; i < n; i += T) S.idx[S.start[ens_cell(B, S.pos[i])] + S.slot[i]] = (uint16_t)i;
+        for (int c = threadIdx.x; c < ncell; c += T) S.cnt[c] = 0u;
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncell; c += T) {  // members of a cell in index order
+            const int lo = (int)S.start[c], hi = (int)S.start[c + 1];
+            for (int k = lo + 1; k < hi; ++k) {
+                const uint16_t v = S.idx[k];
+                int m = k - 1;
+                while (m >= lo && S.idx[m] > v) {
+                    S.idx[m + 1] = S.idx[m];
+                    --m;
+                }
+                S.idx[m + 1] = v;
+            }
+        }
+        __syncthreads();
+        // 2. pair forces of this CTA's units
+        for (int u = rank + C * warp; u < nunits; u += C * nwarps) {
+            if (last) ens_unit<SMODE, true>(B, S, q, cand, u, lane);
+            else ens_unit<SMODE, false>(B, S, q, cand, u, lane);
+        }
+        __syncthreads();
+        if (C > 1) cl.sync();  // every replica has been read for this step
+        // 3. integrate the particles of this CTA's units
+        const unsigned long long stepn = step0 + (unsigned long long)s + 1ull;  // step of the next force
+        for (int u = rank + C * warp; u < nunits; u += C * nwarps) {
+            const int k0 = (int)S.start[u * kEnsUnitCells];
+            const int k1 = (int)S.start[min((u + 1) * kEnsUnitCells, ncell)];
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const int i = S.idx[k];
+                float4 f = S.f[i];
+                const float4 x = S.pos[i];
+                if (B.body_mode == 1) {
+                    f.x += B.body[0]; f.y += B.body[1]; f.z += B.body[2];
+                } else if (B.body_mode == 2) {
+                    const float sg = x.y < B.halfL[1] ? 1.0f : -1.0f;
+                    f.x = fmaf(sg, B.body[0], f.x); f.y = fmaf(sg, B.body[1], f.y); f.z = fmaf(sg, B.body[2], f.z);
+                }
+                if (!isfinite(f.x) || !isfinite(f.y) || !isfinite(f.z)) {
+                    atomicOr(B.err, kErrNonFinite);
+                    atomicOr(B.any_err, kErrNonFinite);
+                }
+                if (steps == 0) {
+                    B.frc[i] = f;
+                } else if (last) {
+                    // phase 2 only: the full-step velocity
+                    const float4 uo = LHALF ? S.u[i] : S.vh[i];
+                    B.pos[i] = x;
+                    B.vel[i] = make_float4(fmaf(B.half_dt, f.x, uo.x), fmaf(B.half_dt, f.y, uo.y),
+                                           fmaf(B.half_dt, f.z, uo.z), 0.0f);
+                    B.frc[i] = f;
+                } else {
+                    // phase 2 of this step and phase 1 of the next:
+                    //   v = u + dt/2 f;  u' = v + dt/2 f;  v~ = v + lambda dt f;  x' = x + dt u'
+                    const float4 uo = LHALF ? S.u[i] : S.vh[i];
+                    const float sig = __uint_as_float(signature(__ldg(B.tag + i), (uint32_t)stepn, B.key));
+                    float ux, uy, uz, tx, ty, tz;
+                    if (LHALF) {
+                        ux = fmaf(B.dt, f.x, uo.x); uy = fmaf(B.dt, f.y, uo.y); uz = fmaf(B.dt, f.z, uo.z);
+                        tx = ux; ty = uy; tz = uz;
+                    } else {
+                        const float vx = fmaf(B.half_dt, f.x, uo.x), vy = fmaf(B.half_dt, f.y, uo.y),
+                                    vz = fmaf(B.half_dt, f.z, uo.z);
+                        ux = fmaf(B.half_dt, f.x, vx); uy = fmaf(B.half_dt, f.y, vy); uz = fmaf(B.half_dt, f.z, vz);
+                        tx = fmaf(B.lambda_dt, f.x, vx); ty = fmaf(B.lambda_dt, f.y, vy);
+                        tz = fmaf(B.lambda_dt, f.z, vz);
+                    }
+                    float4 xn = x;
+                    xn.x = ens_wrap(fmaf(B.dt, ux, x.x), B.L[0], invL[0]);
+                    xn.y = ens_wrap(fmaf(B.dt, uy, x.y), B.L[1], invL[1]);
+                    xn.z = ens_wrap(fmaf(B.dt, uz, x.z), B.L[2], invL[2]);
+                    const float4 un = make_float4(tx, ty, tz, sig);
+                    const float4 vhn = make_float4(ux, uy, uz, 0.0f);
+                    for (int r = 0; r < C; ++r) {
+                        float4 *pp = C > 1 ? cl.map_shared_rank(S.pos, r) : S.pos;
+                        float4 *up = C > 1 ? cl.map_shared_rank(S.u, r) : S.u;
+                        pp[i] = xn;
+                        up[i] = un;
+                        if (!LHALF) {
+                            float4 *hp = C > 1 ? cl.map_shared_rank(S.vh, r) : S.vh;
+                            hp[i] = vhn;
+                        }
+                    }
+                }
+            }
+        }
+        if (!last) {
+            if (C > 1) cl.sync();  // every replica holds the new state
+            else __syncthreads();
+        }
+    }
+    // no CTA leaves while another may still address its shared memory
+    if (C > 1) cl.sync();
+}
+
+// Per box: sum v^2, virial (the w of the forces), momentum; FP64, fixed order.
+__global__ void __launch_bounds__(kObsThreads) k_ens_observe(const EnsBox *__restrict__ boxes, double *out)
+{
+    __shared__ double sh[5][kObsThreads / 32];
+    const EnsBox &B = boxes[blockIdx.x];
+    double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < B.n; i += kObsThreads) {
+        const float4 v = B.vel[i], f = B.frc[i];
+        a[0] += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
+        a[1] += (double)f.w;
+        a[2] += v.x;
+        a[3] += v.y;
+        a[4] += v.z;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        double x = a[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) sh[k][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double s = 0.0;
+        for (int w = 0; w < kObsThreads / 32; ++w) s += sh[threadIdx.x][w];
+        out[8 * blockIdx.x + threadIdx.x] = s;
+    }
+}
+
+using EnsKernel = void (*)(const EnsBox *, int);
+
+EnsKernel pick(bool lhalf, int s_mode)
+{
+    switch (s_mode) {
+    case 1: return lhalf ? k_ens_run<true, 1> : k_ens_run<false, 1>;
+    case 2: return lhalf ? k_ens_run<true, 2> : k_ens_run<false, 2>;
+    case 3: return lhalf ? k_ens_run<true, 3> : k_ens_run<false, 3>;
+    default: return lhalf ? k_ens_run<true, 0> : k_ens_run<false, 0>;
+    }
+}
+
+size_t g_limit = 0;
+std::once_flag g_once;
+
+void init_attributes()
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    size_t limit = (size_t)optin;
+    for (int l = 0; l < 2; ++l)
+        for (int m = 0; m < 4; ++m) {
+            cudaFuncAttributes fa;
+            if (cudaFuncGetAttributes(&fa, pick(l == 1, m)) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+            limit = std::min(limit, (size_t)optin - fa.sharedSizeBytes);
+        }
+    for (int l = 0; l < 2; ++l)
+        for (int m = 0; m < 4; ++m)
+            if (cudaFuncSetAttribute(pick(l == 1, m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+    g_limit = limit;
+}
+
+cudaLaunchConfig_t config_for(int nb, int threads, int cluster, size_t smem, cudaStream_t s, cudaLaunchAttribute *at)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nb * cluster), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+}  // namespace
+
+size_t ensemble_smem_limit()
+{
+    std::call_once(g_once, init_attributes);
+    return g_limit;
+}
+
+int ensemble_max_clusters(bool lhalf, int s_mode, int threads, int cluster, size_t smem)
+{
+    if (ensemble_smem_limit() == 0 || smem > g_limit) return 0;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = config_for(cluster, threads, cluster, smem, nullptr, at);
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, pick(lhalf, s_mode), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return num;
+}
+
+cudaError_t launch_ensemble(const EnsBox *boxes, int nb, bool lhalf, int s_mode, int threads, int cluster,
+                            size_t smem, cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    if (ensemble_smem_limit() == 0 || smem > g_limit || threads < 32 || threads > kEnsMaxThreads ||
+        threads % 32 != 0 || cluster < 1 || cluster > kEnsMaxCluster)
+        return cudaErrorInvalidValue;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = config_for(nb, threads, cluster, smem, s, at);
+    return cudaLaunchKernelEx(&cfg, pick(lhalf, s_mode), boxes, cluster);
+}
+
+cudaError_t launch_ensemble_observe(const EnsBox *boxes, int nb, double *out, cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    k_ens_observe<<<nb, kObsThreads, 0, s>>>(boxes, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dpd

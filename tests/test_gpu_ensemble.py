@@ -1,0 +1,210 @@
+"""Ensemble kernel (include/dpd_ensemble.h): many small boxes, one cluster
+of CTAs per box, the box resident in shared memory for a chunk of steps.
+
+Against the FP64 oracle on the same seeded inputs: the initial force within
+1e-4 of the RMS force (max over particles and components), for one and two
+species, the general weight exponent and lambda != 1/2; a short trajectory
+within the tolerances of the engine's own trajectory test.  Determinism: a
+box's trajectory is bit-identical whatever the cluster size, block size and
+the other boxes of the launch.  Physics: temperature and pressure of a long
+run agree with the neighbour-list engine within statistical error."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1311_0402_gb300 as dpd
+import workloads
+from gpu_util import force_error, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _fluid(L, seed, rho=3.0, kT=1.0):
+    box = (float(L),) * 3
+    n = workloads.n_particles(box, rho)
+    x, v = workloads.uniform_fluid(box, n, kT, seed)[:2]
+    return box, x, v
+
+
+def _add(ens, box, x, v, a=25.0, gamma=4.5, s=1.0, lam=0.5, seed=42, step=0, species=None, dt=0.01, **kw):
+    a_ij = np.atleast_2d(np.asarray(a, np.float64))
+    return ens.add(box, a_ij, gamma, 1.0, 1.0, s, dt, x, v, species=species, step=step, lam=lam, seed=seed, **kw)
+
+
+@pytest.mark.parametrize("case", ["one_species", "two_species", "s_quarter", "lambda_065"])
+def test_initial_force_matches_oracle(case):
+    box, x, v = _fluid(8, 101)
+    a, s, lam, sp = 25.0, 1.0, 0.5, None
+    if case == "two_species":
+        a = [[25.0, 60.0], [60.0, 25.0]]
+        sp = (np.arange(x.shape[0]) % 2).astype(np.int32)
+    elif case == "s_quarter":
+        s = 0.25
+    elif case == "lambda_065":
+        lam = 0.65
+    ens = dpd.Ensemble()
+    i = _add(ens, box, x, v, a=a, s=s, lam=lam, step=9, species=sp)
+    x32, v32, step = ens.state(i)
+    assert step == 9
+    o = oracle.System(box, a, 4.5, 1.0, 1.0, s, 0.01, lam=lam, seed=42, cut_fp32=True)
+    fo, vir = o.forces(x32, v32, species=sp, step=9)
+    fg = ens.forces(i)
+    err, rms = force_error(fg, fo)
+    assert err < FORCE_TOL, (err, rms)
+    ob = ens.observables(i)
+    assert abs(ob["virial"] - vir) < 1e-5 * abs(vir)
+    assert np.abs(ob["momentum"] - v32.sum(0)).max() < 1e-9 * np.abs(v32).sum()
+    ens.close()
+
+
+@pytest.mark.parametrize("lam", [0.5, 0.65])
+def test_short_trajectory_matches_oracle(lam):
+    box, x, v = _fluid(9, 102)
+    ens = dpd.Ensemble(cluster=4)
+    i = _add(ens, box, x, v, lam=lam, step=3)
+    x32, v32, _ = ens.state(i)
+    o = oracle.System(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, lam=lam, seed=42, cut_fp32=True)
+    f0, _ = o.forces(x32, v32, step=3)
+    res = o.run(x32, v32, 2, step=3, f=f0)
+    ens.step(2)
+    ens.sync()
+    xg, vg, sg = ens.state(i)
+    assert sg == 5 and res["step"] == 5
+    dx = xg - res["x"]
+    dx -= np.asarray(box) * np.round(dx / np.asarray(box))
+    assert np.abs(dx).max() < 1e-5
+    err, _ = force_error(ens.forces(i), res["f"])
+    assert err < 1e-3, err
+    assert np.abs(vg - res["v"]).max() < 1e-3
+    ens.close()
+
+
+def _run(boxes, threads, cluster, steps, chunks=2):
+    ens = dpd.Ensemble(threads=threads, cluster=cluster)
+    ids = [_add(ens, b["box"], b["x"], b["v"], a=b["a"], gamma=b["gamma"], seed=b["seed"]) for b in boxes]
+    for _ in range(chunks):
+        ens.step(steps)
+    ens.sync()
+    out = [(ens.state(i), ens.observables(i)) for i in ids]
+    ens.close()
+    return out
+
+
+def test_bit_identical_across_shapes_and_mixes():
+    boxes = workloads.serving_stream(5, seed=21, L_range=(6, 10), steps_range=(10, 10))
+    alone = _run(boxes[:1], 128, 1, 25)[0]
+    for threads, cluster in ((256, 2), (512, 8), (256, 4)):
+        mixed = _run(boxes, threads, cluster, 25)
+        (x, v, step), ob = mixed[0]
+        assert step == 50
+        assert np.array_equal(x, alone[0][0]) and np.array_equal(v, alone[0][1]), (threads, cluster)
+        assert ob["temperature"] == alone[1]["temperature"] and ob["virial"] == alone[1]["virial"]
+
+
+def test_per_box_steps_and_ids():
+    boxes = workloads.serving_stream(3, seed=22, L_range=(6, 8), steps_range=(10, 10))
+    ens = dpd.Ensemble()
+    ids = [_add(ens, b["box"], b["x"], b["v"], seed=b["seed"]) for b in boxes]
+    ens.step([5, 0, 12], ids=ids)
+    ens.step(3, ids=[ids[1]])
+    ens.sync()
+    assert [ens.state(i)[2] for i in ids] == [5, 3, 12]
+    # box 2 run alone in one 12-step chunk: the same state (a chunk boundary
+    # rounds phase 2 and the next phase 1 separately, so the split must match)
+    ens2 = dpd.Ensemble()
+    j = _add(ens2, boxes[2]["box"], boxes[2]["x"], boxes[2]["v"], seed=boxes[2]["seed"])
+    ens2.step(12)
+    ens2.sync()
+    assert np.array_equal(ens2.state(j)[0], ens.state(ids[2])[0])
+    ens.remove(ids[0])
+    assert ens.info()[0] == 2
+    with pytest.raises(dpd.DPDError):
+        ens.state(ids[0])
+    ens.close()
+    ens2.close()
+
+
+def test_thermodynamics_match_the_engine():
+    """rho = 3, a = 25, kT = 1 in an L = 10 box: temperature and pressure over
+    a long run, ensemble kernel vs the neighbour-list engine (independent
+    random streams, so statistical agreement)."""
+    box, x, v = _fluid(10, 103)
+    ens = dpd.Ensemble()
+    i = _add(ens, box, x, v)
+    sim = dpd.Sim(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, deterministic=1)
+    sim.set_state(x, v)
+    ens.step(500)
+    sim.step(500)
+    te, pe, ts, ps = [], [], [], []
+    for _ in range(60):
+        ens.step(20)
+        sim.step(20)
+        ens.sync()
+        a, b = ens.observables(i), sim.observables()
+        te.append(a["temperature"]); pe.append(a["pressure"])
+        ts.append(b["temperature"]); ps.append(b["pressure"])
+    assert abs(np.mean(te) - 1.0) < 0.03 and 22.5 < np.mean(pe) < 25.0
+    assert abs(np.mean(te) - np.mean(ts)) < 0.015
+    assert abs(np.mean(pe) - np.mean(ps)) < 0.01 * np.mean(ps)
+    assert abs(ens.observables(i)["momentum"]).max() < 1e-2
+    ens.close()
+    sim.close()
+
+
+def test_reverse_poiseuille_body_force():
+    box, x, v = _fluid(8, 104)
+    ens = dpd.Ensemble()
+    i = _add(ens, box, x, v, body_mode=2, body=(0.3, 0.0, 0.0))
+    ens.step(400)
+    ens.sync()
+    xg, vg, _ = ens.state(i)
+    low = xg[:, 1] < box[1] / 2
+    assert vg[low, 0].mean() > 0.1 and vg[~low, 0].mean() < -0.1
+    ens.close()
+
+
+def test_limits_and_errors():
+    assert dpd.dpd_ensemble_fits((10.0,) * 3, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, 3000)
+    assert not dpd.dpd_ensemble_fits((20.0,) * 3, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, 24000)
+    assert not dpd.dpd_ensemble_fits((2.9,) * 3, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, 10)
+    ens = dpd.Ensemble()
+    box, x, v = _fluid(6, 105)
+    bad = x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(dpd.DPDError) as e:
+        _add(ens, box, bad, v)
+    assert e.value.status == 1
+    with pytest.raises(dpd.DPDError) as e:
+        _add(ens, (20.0,) * 3, np.zeros((24000, 3)), np.zeros((24000, 3)))
+    assert e.value.status == 1
+    assert ens.info() == (0, 0)
+    with pytest.raises(dpd.DPDError):
+        ens.step(5, ids=[7])
+    ens.close()
+
+
+def test_tuner_picks_a_measured_shape():
+    boxes = workloads.serving_stream(24, seed=23, L_range=(6, 10), steps_range=(10, 10))
+    ens = dpd.Ensemble()
+    ids = [_add(ens, b["box"], b["x"], b["v"], seed=b["seed"]) for b in boxes]
+    before = [ens.state(i)[0] for i in ids[:3]]
+    table = ens.tune(steps=10)
+    finite = {k: t for k, t in table.items() if np.isfinite(t)}
+    assert finite and all(t > 0 for t in finite.values())
+    threads, cluster = ens.config()
+    assert any(t in (128, 256, 512) for t in threads)
+    # tuning runs on copies: the boxes have not moved
+    for i, x0 in zip(ids[:3], before):
+        x1, _, step = ens.state(i)
+        assert step == 0 and np.array_equal(x0, x1)
+    ens.step(10)
+    ens.sync()
+    assert ens.state(ids[0])[2] == 10
+    ens.close()
