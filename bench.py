@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--serve-boxes", type=int, default=512)
     ap.add_argument("--serve-active", type=int, default=32)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--small-boxes", type=int, default=256,
+                    help="boxes of the ensemble-kernel leg (0 skips it)")
     ap.add_argument("--no-tune", action="store_true", help="skip the skin tuner's measurement of the 3M system")
     ap.add_argument("--ablations", action="store_true",
                     help="also time the atomic-insertion list builder against the ballot one (Table 2)")
@@ -268,30 +270,45 @@ def run_serving(args):
         return srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
                           b["steps"], seed=b["seed"], skin=b["skin"])
 
-    # (2) saturated: everything queued at once
-    srv = dpd.Server(max_active=args.serve_active, chunk_steps=100)
-    t0 = srv.now()
-    tickets = [submit(srv, b) for b in boxes]
-    res = [srv.wait(t, timeout_s=3600.0, state=True) for t in tickets]
-    t_sat = max(r["t_done"] for r in res) - t0
-    bad = sum(1 for r in res if r["status"] != 0)
-    srv.close()
+    # (2) saturated: everything queued at once, every box on its own handle;
+    # then the same with the boxes that fit routed to the ensemble kernel
+    def saturated(ensemble):
+        srv = dpd.Server(max_active=args.serve_active, chunk_steps=100, ensemble=ensemble)
+        t0 = srv.now()
+        tickets = [submit(srv, b) for b in boxes]
+        res = [srv.wait(t, timeout_s=3600.0, state=True) for t in tickets]
+        srv.close()
+        return max(r["t_done"] for r in res) - t0, sum(1 for r in res if r["status"] != 0)
+
+    t_sat, bad = saturated(0)
+    t_sat_e, bad_e = saturated(1)
+    bad += bad_e
     # (3) Poisson arrivals at 1.2x the one-box-at-a-time capacity
     rate = 1.2 * len(boxes) / t_seq
     arrivals = workloads.serving_stream(args.serve_boxes, with_state=False, rate=rate)
-    srv = dpd.Server(max_active=args.serve_active, chunk_steps=100)
-    t0 = srv.now()
-    tickets = []
-    for b, a in zip(boxes, arrivals):
-        dt = a["t_arrive"] - (srv.now() - t0)
-        if dt > 0:
-            time.sleep(dt)
-        tickets.append(submit(srv, b))
-    res = [srv.wait(t, timeout_s=3600.0, state=False) for t in tickets]
-    srv.close()
-    bad += sum(1 for r in res if r["status"] != 0)
-    ttc = np.array([r["t_done"] - r["t_submit"] for r in res])
-    span = max(r["t_done"] for r in res) - t0
+
+    def poisson(ensemble):
+        srv = dpd.Server(max_active=args.serve_active, chunk_steps=100, ensemble=ensemble)
+        t0 = srv.now()
+        tickets = []
+        for b, a in zip(boxes, arrivals):
+            dt = a["t_arrive"] - (srv.now() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(submit(srv, b))
+        res = [srv.wait(t, timeout_s=3600.0, state=False) for t in tickets]
+        srv.close()
+        ttc = np.array([r["t_done"] - r["t_submit"] for r in res])
+        span = max(r["t_done"] for r in res) - t0
+        return {"rate_boxes_per_s": rate, "value": total / span, "unit": UNIT, "wall_s": span,
+                "p50_s": float(np.percentile(ttc, 50)), "p99_s": float(np.percentile(ttc, 99)),
+                "arrival": "Poisson, 1.2x the one-box-at-a-time capacity"}, sum(1 for r in res if r["status"] != 0)
+
+    pois, b1 = poisson(1)
+    pois_plain, b2 = poisson(0)
+    bad += b1 + b2
+    n_ens = sum(1 for b in boxes if dpd.dpd_ensemble_fits(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"],
+                                                          b["dt"], b["n"]))
     return {
         "metric": "batched-ensemble time-to-completion (p50 / p99) and particle-steps/s",
         "boxes": len(boxes), "particle_steps": total, "failed": bad,
@@ -299,12 +316,84 @@ def run_serving(args):
                     "particles), a in [15,40], gamma in [3,6], kT=1, dt=0.01, 500-5000 steps each",
         "skin_by_box_length": {"L %d-%d" % (lo, min(hi, 30)): {"skin": best, "ms_per_step_tried": table}
                                for (lo, hi), (best, table) in tuned.items()},
+        "boxes_fitting_the_ensemble_kernel": n_ens,
         "one_box_at_a_time": {"value": total / t_seq, "unit": UNIT, "wall_s": t_seq},
-        "saturated": {"value": total / t_sat, "unit": UNIT, "wall_s": t_sat,
-                      "vs_one_box_at_a_time": t_seq / t_sat, "max_active": args.serve_active},
-        "poisson": {"rate_boxes_per_s": rate, "value": total / span, "unit": UNIT, "wall_s": span,
-                    "p50_s": float(np.percentile(ttc, 50)), "p99_s": float(np.percentile(ttc, 99)),
-                    "arrival": "Poisson, 1.2x the one-box-at-a-time capacity"},
+        "saturated": {"value": total / t_sat_e, "unit": UNIT, "wall_s": t_sat_e,
+                      "vs_one_box_at_a_time": t_seq / t_sat_e, "max_active": args.serve_active,
+                      "routing": "boxes that fit run in the ensemble kernel, the others on their own handles"},
+        "saturated_handles_only": {"value": total / t_sat, "unit": UNIT, "wall_s": t_sat,
+                                   "vs_one_box_at_a_time": t_seq / t_sat, "max_active": args.serve_active},
+        "poisson": dict(pois, routing="boxes that fit run in the ensemble kernel"),
+        "poisson_handles_only": pois_plain,
+    }
+
+
+def run_small_boxes(args):
+    """Ensemble kernel leg: a seeded stream of small boxes (L uniform in
+    6..10, rho = 3, 500-5000 steps), all resident at once, advanced in chunks
+    of 100 steps by the ensemble kernel after its autotuner has chosen threads
+    per CTA and CTAs per box; against the serving loop running the same boxes
+    each on its own handle, and the plain path one box at a time on a sample."""
+    import paper_1311_0402_gb300 as dpd
+    import workloads
+    boxes = workloads.serving_stream(args.small_boxes, seed=workloads.BASE_SEED + 9, L_range=(6, 10),
+                                     with_state=True)
+    total = float(sum(b["n"] * b["steps"] for b in boxes))
+    ens = dpd.Ensemble()
+    ids = [ens.add(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"], seed=b["seed"])
+           for b in boxes]
+    table = ens.tune(steps=20)
+    ens.sync()
+    threads, cluster = ens.config()
+    left = {i: b["steps"] for i, b in zip(ids, boxes)}
+    done = []
+    t0 = time.perf_counter()
+    while left:
+        ks = list(left)
+        st = [min(100, left[k]) for k in ks]
+        ens.step(st, ids=ks)
+        ens.sync()
+        now = time.perf_counter() - t0
+        for k, c in zip(ks, st):
+            left[k] -= c
+            if left[k] == 0:
+                del left[k]
+                done.append(now)
+    t_ens = time.perf_counter() - t0
+    ens.close()
+    srv = dpd.Server(max_active=args.serve_active, chunk_steps=100)
+    t1 = srv.now()
+    tickets = [srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"], b["steps"],
+                          seed=b["seed"]) for b in boxes]
+    res = [srv.wait(t, timeout_s=3600.0, state=False) for t in tickets]
+    srv.close()
+    tt = np.array([r["t_done"] - t1 for r in res])
+    # one box at a time on every 8th box (the plain path is slow here)
+    sample = boxes[::8]
+    t2 = time.perf_counter()
+    for b in sample:
+        sim = dpd.Sim(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], seed=b["seed"],
+                      conditional_rebuild=0)
+        sim.set_state(b["x"], b["v"])
+        sim.step(b["steps"])
+        sim.observables()
+        sim.state()
+        sim.close()
+    t_seq = time.perf_counter() - t2
+    seq_total = float(sum(b["n"] * b["steps"] for b in sample))
+    done = np.array(done)
+    return {
+        "workload": "%d seeded periodic cubes, L uniform in 6..10 (648..3000 particles), rho=3, a in [15,40], "
+                    "gamma in [3,6], kT=1, dt=0.01, 500-5000 steps each, all submitted at t=0" % len(boxes),
+        "particle_steps": total,
+        "ensemble_kernel": {"value": total / t_ens, "unit": UNIT, "wall_s": t_ens,
+                            "p50_s": float(np.percentile(done, 50)), "p99_s": float(np.percentile(done, 99)),
+                            "threads_per_cta_by_class": threads, "ctas_per_box_by_class": cluster,
+                            "tuner_ms_per_step_last_class": {"%dx%d" % k: v for k, v in table.items()}},
+        "serving_loop_own_handles": {"value": total / float(tt.max()), "unit": UNIT, "wall_s": float(tt.max()),
+                                     "p50_s": float(np.percentile(tt, 50)), "p99_s": float(np.percentile(tt, 99)),
+                                     "max_active": args.serve_active},
+        "one_box_at_a_time": {"value": seq_total / t_seq, "unit": UNIT, "sample": "every 8th box"},
     }
 
 
@@ -493,6 +582,8 @@ def main():
     sim.close()
     if rank == 0 and ws == 1 and not args.no_serving:
         line["batched"] = run_serving(args)
+        if args.small_boxes > 0:
+            line["batched"]["small_boxes"] = run_small_boxes(args)
     if rank == 0 and ws == 1 and args.ablations:
         line["list_builder_ablation"] = run_list_ablation()
         line["reorder_ablation"] = run_reorder_ablation()

@@ -26,6 +26,7 @@
 #define DPD_SERVER_H
 
 #include "dpd.h"
+#include "dpd_ensemble.h"
 
 #ifdef __cplusplus
 extern "C" {
@@ -43,6 +44,12 @@ typedef struct {
                                   when the server is created */
     dpd_options box_options;   /* run options of every box (the seed and the stream are
                                   taken per box: each box gets its own stream) */
+    int32_t ensemble;          /* 1: boxes that fit the ensemble kernel (dpd_ensemble.h:
+                                  about 4,000 particles or fewer, each side >= 3 rc) run
+                                  there instead, all of them advanced together by one
+                                  launch per size class and chunk, driven by one more
+                                  worker thread; 0 (default): every box on its own handle */
+    int32_t ensemble_slots;    /* boxes resident in the ensemble at once (default 1024) */
 } dpd_server_options;
 
 /* One box to run: the arguments of dpd_create + dpd_set_state + dpd_step.
@@ -73,7 +80,11 @@ typedef struct {
     dpd_obs obs;               /* observables of the final state */
 } dpd_result;
 
-/* Defaults: max_active 32, 4 workers, chunk_steps 100, budget 60 % of free memory,
+/* Results of boxes run by the ensemble kernel are bit-identical to the same box
+ * run alone through dpd_ensemble.h in the same chunks of chunk_steps, and agree
+ * with dpd.h's engine to FP32 rounding (a different summation order).
+ *
+ * Defaults: max_active 32, 4 workers, chunk_steps 100, budget 60 % of free memory,
  * dpd_default_options() for the boxes with conditional_rebuild = 0 (for
  * boxes of a few thousand particles the plain chain launches are cheaper).
  * For more than 8 boxes to run concurrently, set CUDA_DEVICE_MAX_CONNECTIONS

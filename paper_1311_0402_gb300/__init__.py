@@ -81,6 +81,8 @@ class dpd_server_options(ctypes.Structure):
         ("chunk_steps", ctypes.c_int32),
         ("mem_budget_bytes", ctypes.c_double),
         ("box_options", dpd_options),
+        ("ensemble", ctypes.c_int32),
+        ("ensemble_slots", ctypes.c_int32),
     ]
 
 
@@ -565,9 +567,11 @@ class Server:
     """Continuous batching of independent boxes (include/dpd_server.h)."""
 
     def __init__(self, max_active=32, chunk_steps=100, mem_budget_bytes=0.0, skin=0.3, deterministic=0,
-                 graph_steps=8, lam=0.5, conditional_rebuild=0, workers=4):
+                 graph_steps=8, lam=0.5, conditional_rebuild=0, workers=4, ensemble=0, ensemble_slots=1024):
         o = dpd_server_options()
         lib().dpd_server_default_options(ctypes.byref(o))
+        o.ensemble = 1 if ensemble else 0
+        o.ensemble_slots = ensemble_slots
         o.max_active = max_active
         o.workers = workers
         o.chunk_steps = chunk_steps

@@ -7,7 +7,9 @@
 // checks finished chunks (dpd_sync), and admits queued boxes first-fit by
 // estimated device memory whenever a box finishes.  Device memory of the
 // handles is stream-ordered, so creating or freeing one box never waits for
-// the others.
+// the others.  With the ensemble option, boxes small enough for the ensemble
+// kernel (dpd_ensemble.h) go to one more worker instead, which keeps them all
+// in one dpd_ensemble and advances every one of them a chunk per launch.
 #include "dpd_server.h"
 #include "dpd_internal.cuh"
 
@@ -41,6 +43,7 @@ struct Job {
     uint64_t steps = 0;
     double skin = 0;        // 0: the server's box_options.skin
     double est_bytes = 0;
+    bool ens = false;       // runs in the ensemble kernel
     double t_submit = 0;
     double t_admit = 0;     // stamped under the server's lock when taken from the queue
 };
@@ -75,6 +78,31 @@ double estimate_bytes(const Job &j, const dpd_options &o)
     return (double)j.n * 320.0 + groups * 32.0 * cap * 4.0 + ncell * 160.0 + 4.0 * 1024 * 1024;
 }
 
+// Device bytes of a box in the ensemble: state, tags and indices (56 B per
+// particle), its staging at upload (48 B per particle) and a small allowance.
+double estimate_ensemble_bytes(const Job &j) { return (double)j.n * 104.0 + 64.0 * 1024; }
+
+dpd_box_params box_params_of(const Job &j, const dpd_options &o)
+{
+    dpd_box_params p;
+    std::memset(&p, 0, sizeof(p));
+    for (int a = 0; a < 3; ++a) {
+        p.box[a] = j.box[a];
+        p.body_force[a] = o.body_force[a];
+    }
+    p.n_species = j.n_species;
+    p.a_ij = j.a.data();
+    p.gamma = j.gamma;
+    p.kT = j.kT;
+    p.rc = j.rc;
+    p.s = j.s;
+    p.dt = j.dt;
+    p.lambda = o.lambda;
+    p.seed = j.seed;
+    p.body_force_mode = o.body_force_mode;
+    return p;
+}
+
 }  // namespace
 
 struct dpd_server {
@@ -92,6 +120,7 @@ struct dpd_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     std::vector<std::thread> workers;
+    std::thread ens_worker;
     std::string err;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -174,13 +203,18 @@ void worker_loop(dpd_server *S, int slots)
         bool stopping = false;
         {
             std::unique_lock<std::mutex> lk(S->m);
-            if (active.empty() && S->pending.empty() && !S->stop)
-                S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            bool mine = false;  // a queued box this kind of worker runs
+            for (const Job &j : S->pending) mine = mine || !j.ens;
+            if (active.empty() && !mine && !S->stop) S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
             stopping = S->stop;
             if (!stopping) {
                 int looked = 0;
                 for (auto it = S->pending.begin();
                      it != S->pending.end() && (int)(active.size() + admit.size()) < slots && looked < 16;) {
+                    if (it->ens) {
+                        ++it;
+                        continue;
+                    }
                     if (S->mem_used + it->est_bytes <= S->budget) {
                         S->mem_used += it->est_bytes;
                         S->running += 1;
@@ -255,6 +289,154 @@ void worker_loop(dpd_server *S, int slots)
     S->pending.clear();
 }
 
+// The ensemble worker: admits the boxes routed to the ensemble kernel (first
+// fit by memory, in submission order), advances all of them by one chunk per
+// pass -- one launch per size class -- and reads back the finished ones.
+void ensemble_loop(dpd_server *S)
+{
+    cudaSetDevice(S->device);
+    struct EJob {
+        Job job;
+        int32_t id = -1;
+        uint64_t left = 0;
+    };
+    dpd_ensemble *E = nullptr;
+    dpd_status est = dpd_ensemble_create(&E, nullptr);
+    std::string emsg = est == DPD_OK ? "" : std::string("ensemble: ") + dpd_ensemble_last_error(nullptr);
+    std::vector<EJob> active;
+    auto done_job = [&](EJob &ej, dpd_status st, const std::string &msg) {
+        Done d;
+        std::memset(&d.res, 0, sizeof(d.res));
+        d.res.ticket = ej.job.ticket;
+        d.res.status = st;
+        d.res.n = ej.job.n;
+        d.res.steps = ej.job.steps;
+        d.res.t_submit = ej.job.t_submit;
+        d.res.t_admit = ej.job.t_admit;
+        std::string m2 = msg;
+        if (st == DPD_OK && ej.id >= 0) {
+            d.x.resize(3 * (size_t)ej.job.n);
+            d.v.resize(3 * (size_t)ej.job.n);
+            dpd_status s2 = dpd_ensemble_observables(E, ej.id, &d.res.obs);
+            if (s2 == DPD_OK) s2 = dpd_ensemble_get_state(E, ej.id, d.x.data(), d.v.data(), nullptr);
+            if (s2 != DPD_OK) {
+                d.res.status = s2;
+                m2 = dpd_ensemble_last_error(E);
+            }
+        }
+        if (E && ej.id >= 0) dpd_ensemble_remove(E, ej.id);
+        d.res.t_done = S->now();
+        {
+            std::lock_guard<std::mutex> lk(S->m);
+            S->done[ej.job.ticket] = std::move(d);
+            S->running -= 1;
+            S->mem_used -= ej.job.est_bytes;
+            if (!m2.empty()) S->err = "ticket " + std::to_string(ej.job.ticket) + ": " + m2;
+        }
+        S->cv_done.notify_all();
+    };
+    const int slots = S->opt.ensemble_slots;
+    for (;;) {
+        std::vector<Job> admit;
+        bool stopping = false;
+        {
+            std::unique_lock<std::mutex> lk(S->m);
+            bool any = false;
+            for (const Job &j : S->pending) any = any || j.ens;
+            if (active.empty() && !any && !S->stop) S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            stopping = S->stop;
+            if (!stopping) {
+                int looked = 0;
+                for (auto it = S->pending.begin();
+                     it != S->pending.end() && (int)(active.size() + admit.size()) < slots && looked < 16;) {
+                    if (!it->ens) {
+                        ++it;
+                        continue;
+                    }
+                    if (S->mem_used + it->est_bytes <= S->budget) {
+                        S->mem_used += it->est_bytes;
+                        S->running += 1;
+                        it->t_admit = S->now();
+                        admit.push_back(std::move(*it));
+                        it = S->pending.erase(it);
+                    } else {
+                        ++it;
+                        ++looked;
+                    }
+                }
+            }
+        }
+        if (stopping) break;
+        for (Job &j : admit) {
+            EJob ej;
+            ej.job = std::move(j);
+            ej.left = ej.job.steps;
+            dpd_status st = est;
+            if (st == DPD_OK) {
+                const dpd_box_params p = box_params_of(ej.job, S->opt.box_options);
+                st = dpd_ensemble_add(E, &p, ej.job.n, ej.job.x.data(), ej.job.v.data(),
+                                      ej.job.species.empty() ? nullptr : ej.job.species.data(), 0, &ej.id);
+            }
+            std::vector<double>().swap(ej.job.x);
+            std::vector<double>().swap(ej.job.v);
+            std::vector<int32_t>().swap(ej.job.species);
+            if (st != DPD_OK) {
+                ej.id = -1;
+                done_job(ej, st, est == DPD_OK ? std::string(dpd_ensemble_last_error(E)) : emsg);
+                continue;
+            }
+            active.push_back(std::move(ej));
+        }
+        if (active.empty()) continue;
+        // one chunk for every resident box
+        std::vector<int32_t> ids, steps;
+        for (const EJob &ej : active) {
+            ids.push_back(ej.id);
+            steps.push_back((int32_t)std::min<uint64_t>(ej.left, (uint64_t)S->opt.chunk_steps));
+        }
+        dpd_status st = dpd_ensemble_step(E, ids.data(), steps.data(), (int32_t)ids.size());
+        if (st == DPD_OK) st = dpd_ensemble_sync(E);
+        if (st != DPD_OK) {
+            // a failed chunk ends every box of it; a CUDA failure ends the ensemble
+            const std::string msg = dpd_ensemble_last_error(E);
+            for (EJob &ej : active) done_job(ej, st, msg);
+            active.clear();
+            if (st == DPD_ERR_CUDA || st == DPD_ERR_TIMEOUT) {
+                dpd_ensemble_destroy(E);
+                E = nullptr;
+                est = dpd_ensemble_create(&E, nullptr);
+                emsg = est == DPD_OK ? "" : std::string("ensemble: ") + dpd_ensemble_last_error(nullptr);
+            }
+            continue;
+        }
+        for (size_t k = 0; k < active.size();) {
+            active[k].left -= (uint64_t)steps[k];
+            if (active[k].left == 0) {
+                done_job(active[k], DPD_OK, "");
+                active.erase(active.begin() + (long)k);
+                steps.erase(steps.begin() + (long)k);
+            } else {
+                ++k;
+            }
+        }
+    }
+    for (EJob &ej : active) done_job(ej, DPD_ERR_STATE, "server stopped");
+    if (E) dpd_ensemble_destroy(E);
+    std::lock_guard<std::mutex> lk(S->m);
+    for (Job &j : S->pending) {
+        Done d;
+        std::memset(&d.res, 0, sizeof(d.res));
+        d.res.ticket = j.ticket;
+        d.res.status = DPD_ERR_STATE;
+        d.res.n = j.n;
+        d.res.steps = j.steps;
+        d.res.t_submit = j.t_submit;
+        d.res.t_done = S->now();
+        S->done[j.ticket] = std::move(d);
+    }
+    S->pending.clear();
+}
+
 }  // namespace
 
 extern "C" {
@@ -271,6 +453,8 @@ void dpd_server_default_options(dpd_server_options *o)
     // small boxes: launching the rebuild chain's early-exit kernels costs
     // less than executing a conditional node's body (measured)
     o->box_options.conditional_rebuild = 0;
+    o->ensemble = 0;
+    o->ensemble_slots = 1024;
 }
 
 dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out)
@@ -279,7 +463,8 @@ dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out)
     *out = nullptr;
     dpd_server_options opt;
     if (o) opt = *o; else dpd_server_default_options(&opt);
-    if (opt.max_active < 1 || opt.workers < 1 || opt.chunk_steps < 1 || !(opt.mem_budget_bytes >= 0.0))
+    if (opt.max_active < 1 || opt.workers < 1 || opt.chunk_steps < 1 || !(opt.mem_budget_bytes >= 0.0) ||
+        opt.ensemble < 0 || opt.ensemble > 1 || (opt.ensemble && opt.ensemble_slots < 1))
         return DPD_ERR_ARG;
     dpd_server *S = new dpd_server();
     S->opt = opt;
@@ -301,6 +486,7 @@ dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out)
         const int slots = opt.max_active / nw + (w < opt.max_active % nw ? 1 : 0);
         S->workers.emplace_back(worker_loop, S, slots);
     }
+    if (opt.ensemble) S->ens_worker = std::thread(ensemble_loop, S);
     *out = S;
     return DPD_OK;
 }
@@ -327,7 +513,11 @@ dpd_status dpd_server_submit(dpd_server *S, const dpd_request *r, uint64_t *tick
     if (r->species) j.species.assign(r->species, r->species + (size_t)r->n);
     j.steps = r->steps;
     j.skin = r->skin;
-    j.est_bytes = estimate_bytes(j, S->opt.box_options);
+    if (S->opt.ensemble) {
+        const dpd_box_params p = box_params_of(j, S->opt.box_options);
+        j.ens = dpd_ensemble_fits(&p, j.n) != 0;
+    }
+    j.est_bytes = j.ens ? estimate_ensemble_bytes(j) : estimate_bytes(j, S->opt.box_options);
     if (j.est_bytes > S->budget) return fail_s(S, DPD_ERR_OOM, "box needs more device memory than the budget");
     {
         std::lock_guard<std::mutex> lk(S->m);
@@ -407,6 +597,7 @@ void dpd_server_destroy(dpd_server *S)
     S->cv_work.notify_all();
     for (std::thread &t : S->workers)
         if (t.joinable()) t.join();
+    if (S->ens_worker.joinable()) S->ens_worker.join();
     delete S;
 }
 

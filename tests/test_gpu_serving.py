@@ -139,3 +139,38 @@ def test_tune_skin_picks_a_measured_candidate():
     assert best in (0.2, 0.4)
     assert np.isfinite(table[0.2]) and np.isfinite(table[0.4]) and np.isinf(table[4.0])
     assert table[best] == min(table.values())
+
+
+def test_ensemble_routing_alone_and_in_the_mix():
+    """With the ensemble option, boxes that fit the ensemble kernel run there:
+    each gives the same bits as the box alone in an ensemble with the same
+    chunks; the larger boxes still run on their own handles, as alone."""
+    need_gpu()
+    boxes = _boxes(10, seed=15, L_range=(6, 14))
+    fits = [dpd.dpd_ensemble_fits(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["n"])
+            for b in boxes]
+    assert any(fits) and not all(fits)
+    srv = dpd.Server(max_active=8, chunk_steps=CHUNK, deterministic=1, ensemble=1)
+    tickets = [srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
+                          b["steps"], seed=b["seed"]) for b in boxes]
+    mixed = [srv.wait(t, timeout_s=300.0) for t in tickets]
+    srv.close()
+    for b, f, r in zip(boxes, fits, mixed):
+        assert r["status"] == 0 and r["obs"]["step"] == b["steps"]
+        if f:
+            ens = dpd.Ensemble()
+            i = ens.add(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
+                        seed=b["seed"])
+            left = b["steps"]
+            while left > 0:
+                ens.step(min(CHUNK, left))
+                left -= min(CHUNK, left)
+            ens.sync()
+            x, v, step = ens.state(i)
+            ob = ens.observables(i)
+            ens.close()
+        else:
+            x, v, step, ob = _alone(b, 1)
+        assert step == b["steps"]
+        assert np.array_equal(r["x"], x) and np.array_equal(r["v"], v), "box L=%g" % b["box"][0]
+        assert r["obs"]["temperature"] == ob["temperature"] and r["obs"]["virial"] == ob["virial"]
