@@ -11,7 +11,8 @@
 //   2. evaluates the pair forces of its share of the cells: work units of
 //      consecutive cells go round-robin to the cluster's CTAs and their warps.
 //      A warp takes a unit cell by cell; the 27-cell stencil of a cell is
-//      gathered once (with each neighbour cell's periodic shift) and every
+//      gathered once (lane l < 27 holds neighbour cell l's periodic shift, a
+//      candidate carries l and fetches the shift by shuffle) and every
 //      owner of the cell tests it 32 candidates at a time.  Hits inside r_c
 //      (the FP32 predicate of the other kernels) go to a per-warp ring in
 //      shared memory, evaluated 32 pairs at a time by the whole warp (Eqs.
@@ -66,12 +67,6 @@ __device__ __forceinline__ int ens_cell(const EnsBox &B, float4 p)
 {
     return (ens_axis(p.z, B.cpl[2], B.nc[2]) * B.nc[1] + ens_axis(p.y, B.cpl[1], B.nc[1])) * B.nc[0] +
            ens_axis(p.x, B.cpl[0], B.nc[0]);
-}
-
-// periodic shift of a neighbour cell along one axis: 0 none, 1 +L, 2 -L
-__device__ __forceinline__ float ens_shift(uint32_t code, float L)
-{
-    return code == 1u ? L : (code == 2u ? -L : 0.0f);
 }
 
 struct EnsPtrs {
@@ -197,18 +192,17 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
         for (int k = ob + lane; k < oe; k += 32) S.f[S.idx[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
         // lane l < 27: neighbour cell l of the stencil, its member range and shift
         const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+        // (the shift stays in the lane's registers; a candidate fetches it by shuffle)
         int len = 0, sbeg = 0;
-        uint32_t code = 0u;
+        float shx = 0.f, shy = 0.f, shz = 0.f;
         if (lane < 27) {
             int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
-            uint32_t kx = 0u, ky = 0u, kz = 0u;
-            if (x < 0) { x += ncx; kx = 2u; } else if (x >= ncx) { x -= ncx; kx = 1u; }
-            if (y < 0) { y += ncy; ky = 2u; } else if (y >= ncy) { y -= ncy; ky = 1u; }
-            if (z < 0) { z += ncz; kz = 2u; } else if (z >= ncz) { z -= ncz; kz = 1u; }
+            if (x < 0) { x += ncx; shx = -B.L[0]; } else if (x >= ncx) { x -= ncx; shx = B.L[0]; }
+            if (y < 0) { y += ncy; shy = -B.L[1]; } else if (y >= ncy) { y -= ncy; shy = B.L[1]; }
+            if (z < 0) { z += ncz; shz = -B.L[2]; } else if (z >= ncz) { z -= ncz; shz = B.L[2]; }
             const int cc = (z * ncy + y) * ncx + x;
             sbeg = (int)S.start[cc];
             len = (int)S.start[cc + 1] - sbeg;
-            code = kx | (ky << 2) | (kz << 4);
         }
         int incl = len;
 #pragma unroll
@@ -222,7 +216,7 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
             __syncwarp();
             if (lane < 27) {
                 const int lo = max(pre, base), hi = min(pre + len, base + kEnsCand);
-                for (int p = lo; p < hi; ++p) cand[p - base] = (uint32_t)S.idx[sbeg + p - pre] | (code << 16);
+                for (int p = lo; p < hi; ++p) cand[p - base] = (uint32_t)S.idx[sbeg + p - pre] | ((uint32_t)lane << 16);
             }
             __syncwarp();
             const int nch = min(kEnsCand, ncand - base);
@@ -231,16 +225,20 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
                 const float4 pi = S.pos[i];
                 for (int t0 = 0; t0 < nch; t0 += 32) {
                     const int t = t0 + lane;
+                    const bool act = t < nch;
+                    const uint32_t e = act ? cand[t] : 0u;
+                    const int sl = (int)(e >> 16);  // stencil cell of the candidate
+                    const float sx = __shfl_sync(0xFFFFFFFFu, shx, sl);
+                    const float sy = __shfl_sync(0xFFFFFFFFu, shy, sl);
+                    const float sz = __shfl_sync(0xFFFFFFFFu, shz, sl);
                     bool hit = false;
                     float dx = 0.f, dy = 0.f, dz = 0.f;
-                    uint32_t j = 0u;
-                    if (t < nch) {
-                        const uint32_t e = cand[t];
-                        j = e & 0xFFFFu;
+                    const uint32_t j = e & 0xFFFFu;
+                    if (act) {
                         const float4 pj = S.pos[j];
-                        dx = __fadd_rn(__fsub_rn(pj.x, pi.x), ens_shift((e >> 16) & 3u, B.L[0]));
-                        dy = __fadd_rn(__fsub_rn(pj.y, pi.y), ens_shift((e >> 18) & 3u, B.L[1]));
-                        dz = __fadd_rn(__fsub_rn(pj.z, pi.z), ens_shift((e >> 20) & 3u, B.L[2]));
+                        dx = __fadd_rn(__fsub_rn(pj.x, pi.x), sx);
+                        dy = __fadd_rn(__fsub_rn(pj.y, pi.y), sy);
+                        dz = __fadd_rn(__fsub_rn(pj.z, pi.z), sz);
                         const float d2 = dist2_rn(dx, dy, dz);
                         hit = (d2 < B.rc2) & (d2 > 0.0f);
                     }
