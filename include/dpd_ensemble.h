@@ -8,10 +8,10 @@
  * advances every listed box a whole chunk of steps: each box is owned by a
  * thread-block cluster of C CTAs, every CTA keeps a replica of the box's
  * positions and velocities in shared memory, and each step bins the box into
- * cells of side >= r_c (Sec. 3.3.1), evaluates the pair forces of its share of
- * the cells (the 27-cell stencil, no neighbour list, no skin), integrates the
- * particles it owns and sends their new state to the other replicas through
- * distributed shared memory.  Nothing goes to device memory between the
+ * cells of side >= r_c (the cell list of Sec. 3.2.3), evaluates the pair
+ * forces of its share of the cells (the 27-cell stencil of Sec. 3.3.1, no
+ * neighbour list, no skin), integrates the particles it owns and sends their
+ * new state to the other replicas through distributed shared memory.  Nothing goes to device memory between the
  * chunk's first and last step.
  *
  * Results: every force is summed in a fixed order (cells in a fixed stencil

@@ -5,15 +5,15 @@
 // Every CTA of a box's cluster holds a replica of the box (positions, the
 // velocity the pair force reads with the particle's signature, the
 // half-kicked velocity when lambda != 1/2) and, each step:
-//   1. bins the box into cells of side >= r_c (Sec. 3.3.1): a counting sort
-//      by shared-memory atomics, then each cell's members put in index order,
-//      so every replica holds the same cell lists;
+//   1. bins the box into cells of side >= r_c (the cell list of Sec. 3.2.3):
+//      a counting sort by shared-memory atomics, then each cell's members put
+//      in index order, so every replica holds the same cell lists;
 //   2. evaluates the pair forces of its share of the cells: work units of
 //      consecutive cells go round-robin to the cluster's CTAs and their warps.
-//      A warp takes a unit cell by cell; the 27-cell stencil of a cell is
-//      gathered once (lane l < 27 holds neighbour cell l's periodic shift, a
-//      candidate carries l and fetches the shift by shuffle) and every
-//      owner of the cell tests it 32 candidates at a time.  Hits inside r_c
+//      A warp takes a unit cell by cell; a cell's 27-cell stencil (Sec.
+//      3.3.1) is gathered once (lane l < 27 holds neighbour cell l's periodic
+//      shift, a candidate carries l and fetches the shift by shuffle) and
+//      every owner of the cell tests it 32 candidates at a time.  Hits inside r_c
 //      (the FP32 predicate of the other kernels) go to a per-warp ring in
 //      shared memory, evaluated 32 pairs at a time by the whole warp (Eqs.
 //      2-9, the TEA hash and Box-Muller Gaussian of Sec. 3.5), and summed per
