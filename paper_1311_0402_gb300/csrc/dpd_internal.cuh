@@ -47,6 +47,7 @@ constexpr int kHaloCells = kHalo * kHalo * kHalo;  // 216
 constexpr uint32_t kErrNbrOverflow = 1u;
 constexpr uint32_t kErrNonFinite = 2u;
 constexpr uint32_t kErrTimeout = 4u;  // a bounded device-side wait ran out
+constexpr uint32_t kErrBadIndex = 8u; // an internal index out of range (reported, the access skipped)
 
 struct DevCtl {
     uint32_t parity;         // live set of the state arrays (pos, vel, vkick, force)

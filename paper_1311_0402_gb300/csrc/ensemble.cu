@@ -518,6 +518,8 @@ dpd_status dpd_ensemble_sync(dpd_ensemble *e)
         if (w) which += (which.empty() ? "" : ", ") + std::to_string(kv.first);
     }
     ENS_TRY(e, cudaMemsetAsync(e->d_any_err, 0, 4, e->stream));
+    if (any & kErrBadIndex)
+        return efail(e, DPD_ERR_STATE, "internal error: a pair index out of range in box(es) " + which);
     return efail(e, DPD_ERR_NONFINITE, "non-finite force in box(es) " + which);
 }
 

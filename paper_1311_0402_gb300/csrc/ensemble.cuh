@@ -12,7 +12,8 @@
 namespace dpd {
 
 constexpr int kEnsQueue = 64;      // hit ring per warp (< 32 pending + 32 new)
-constexpr int kEnsCand = 256;      // candidate buffer per warp (a cell's 27-cell stencil, in rounds)
+constexpr int kEnsSlots = 4;       // candidates per lane per round, held in registers
+constexpr int kEnsCand = 32 * kEnsSlots;  // candidate buffer per warp (a cell's 27-cell stencil, in rounds)
 constexpr int kEnsUnitCells = 8;   // consecutive cells per work unit (one warp, queue flushed at the end)
 constexpr int kEnsMaxCluster = 8;  // portable cluster size
 constexpr int kEnsMaxN = 65535;    // particle indices are 16-bit

@@ -11,13 +11,15 @@
 //   2. evaluates the pair forces of its share of the cells: work units of
 //      consecutive cells go round-robin to the cluster's CTAs and their warps.
 //      A warp takes a unit cell by cell; a cell's 27-cell stencil (Sec.
-//      3.3.1) is gathered once (lane l < 27 holds neighbour cell l's periodic
-//      shift, a candidate carries l and fetches the shift by shuffle) and
-//      every owner of the cell tests it 32 candidates at a time.  Hits inside r_c
-//      (the FP32 predicate of the other kernels) go to a per-warp ring in
-//      shared memory, evaluated 32 pairs at a time by the whole warp (Eqs.
-//      2-9, the TEA hash and Box-Muller Gaussian of Sec. 3.5), and summed per
-//      owner by a segmented shuffle scan (each pair is seen from both sides).
+//      3.3.1) is gathered in rounds of 128 candidates, each lane holding 4 in
+//      registers, and every owner of the cell tests them 32 at a time.  Lane
+//      l < 27 keeps neighbour cell l's periodic shift s; a slot holding a
+//      shifted candidate fetches it by shuffle and forms (x_j - x_i) + s, the
+//      rounding of the other kernels' FP32 predicate.  Hits inside r_c go to
+//      a per-warp ring in shared memory, evaluated 32 pairs at a time by the
+//      whole warp (Eqs. 2-9, the TEA hash and Box-Muller Gaussian of Sec.
+//      3.5), and summed per owner by a segmented shuffle scan (each pair is
+//      seen from both sides).
 //      Within a candidate round every owner's hits are one run of the ring;
 //      the ring is emptied between rounds, so a batch never holds two runs of
 //      one owner;
@@ -121,10 +123,17 @@ __device__ __forceinline__ void ens_batch(const EnsBox &B, const EnsPtrs &S, con
     __syncwarp();
     float fx = 0.f, fy = 0.f, fz = 0.f, fw = 0.f;
     uint32_t owner = 0x10000u + (uint32_t)lane;  // distinct dummy owners for idle lanes
-    if (lane < nb) {
-        const float4 e = q[(head + (uint32_t)lane) & (kEnsQueue - 1)];
-        const uint32_t pk = __float_as_uint(e.w);
-        const uint32_t i = pk >> 16, j = pk & 0xFFFFu;
+    const float4 e = q[(head + (uint32_t)lane) & (kEnsQueue - 1)];
+    const uint32_t pk = __float_as_uint(e.w);
+    const uint32_t i = pk >> 16, j = pk & 0xFFFFu;
+    // an entry naming a particle outside the box would be a bookkeeping fault:
+    // it is reported and skipped, never dereferenced
+    const bool bad = lane < nb && (i >= (uint32_t)B.n || j >= (uint32_t)B.n);
+    if (bad) {
+        atomicOr(B.err, kErrBadIndex);
+        atomicOr(B.any_err, kErrBadIndex);
+    }
+    if (lane < nb && !bad) {
         owner = i;
         const float4 wi = S.u[i], vj = S.u[j];
         const float dx = e.x, dy = e.y, dz = e.z;
@@ -220,36 +229,61 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
             }
             __syncwarp();
             const int nch = min(kEnsCand, ncand - base);
+            // this lane's candidates of the round in registers: base + 32 r + lane.
+            // A slot with a periodic image anywhere in the warp is marked; its
+            // tests add the shift after the difference, (x_j - x_i) + s, the
+            // rounding of the pinned FP32 predicate.
+            float px[kEnsSlots], py[kEnsSlots], pz[kEnsSlots];
+            uint32_t pe[kEnsSlots];  // j | stencil cell << 16
+            uint32_t shifted = 0u;   // warp-uniform: bit r = slot r holds a shifted candidate
+#pragma unroll
+            for (int r = 0; r < kEnsSlots; ++r) {
+                const int t = 32 * r + lane;
+                const bool act = t < nch;
+                const uint32_t e = act ? cand[t] : 0u;
+                const int sl = (int)(e >> 16);
+                // every lane takes part in each shuffle and the ballot
+                const float sx = __shfl_sync(0xFFFFFFFFu, shx, sl);
+                const float sy = __shfl_sync(0xFFFFFFFFu, shy, sl);
+                const float sz = __shfl_sync(0xFFFFFFFFu, shz, sl);
+                const bool sh = act & ((sx != 0.0f) | (sy != 0.0f) | (sz != 0.0f));
+                if (__ballot_sync(0xFFFFFFFFu, sh)) shifted |= 1u << r;
+                pe[r] = e;
+                px[r] = py[r] = pz[r] = 1.0e30f;  // never inside r_c
+                if (act) {
+                    const float4 pj = S.pos[e & 0xFFFFu];
+                    px[r] = pj.x;
+                    py[r] = pj.y;
+                    pz[r] = pj.z;
+                }
+            }
+            const int nslots = (nch + 31) >> 5;
             for (int o = ob; o < oe; ++o) {
                 const uint32_t i = S.idx[o];
                 const float4 pi = S.pos[i];
-                for (int t0 = 0; t0 < nch; t0 += 32) {
-                    const int t = t0 + lane;
-                    const bool act = t < nch;
-                    const uint32_t e = act ? cand[t] : 0u;
-                    const int sl = (int)(e >> 16);  // stencil cell of the candidate
-                    const float sx = __shfl_sync(0xFFFFFFFFu, shx, sl);
-                    const float sy = __shfl_sync(0xFFFFFFFFu, shy, sl);
-                    const float sz = __shfl_sync(0xFFFFFFFFu, shz, sl);
-                    bool hit = false;
-                    float dx = 0.f, dy = 0.f, dz = 0.f;
-                    const uint32_t j = e & 0xFFFFu;
-                    if (act) {
-                        const float4 pj = S.pos[j];
-                        dx = __fadd_rn(__fsub_rn(pj.x, pi.x), sx);
-                        dy = __fadd_rn(__fsub_rn(pj.y, pi.y), sy);
-                        dz = __fadd_rn(__fsub_rn(pj.z, pi.z), sz);
+#pragma unroll
+                for (int r = 0; r < kEnsSlots; ++r) {
+                    if (r < nslots) {
+                        float dx = __fsub_rn(px[r], pi.x);
+                        float dy = __fsub_rn(py[r], pi.y);
+                        float dz = __fsub_rn(pz[r], pi.z);
+                        if ((shifted >> r) & 1u) {
+                            const int sl = (int)(pe[r] >> 16);
+                            dx = __fadd_rn(dx, __shfl_sync(0xFFFFFFFFu, shx, sl));
+                            dy = __fadd_rn(dy, __shfl_sync(0xFFFFFFFFu, shy, sl));
+                            dz = __fadd_rn(dz, __shfl_sync(0xFFFFFFFFu, shz, sl));
+                        }
                         const float d2 = dist2_rn(dx, dy, dz);
-                        hit = (d2 < B.rc2) & (d2 > 0.0f);
-                    }
-                    const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
-                    if (hit)
-                        q[(tail + __popc(m & lt)) & (kEnsQueue - 1)] =
-                            make_float4(dx, dy, dz, __uint_as_float((i << 16) | j));
-                    tail += (uint32_t)__popc(m);
-                    if (tail - head >= 32u) {
-                        ens_batch<SMODE, VIR>(B, S, q, key, head, 32, lane);
-                        head += 32u;
+                        const bool hit = (d2 < B.rc2) & (d2 > 0.0f);
+                        const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
+                        if (hit)
+                            q[(tail + __popc(m & lt)) & (kEnsQueue - 1)] =
+                                make_float4(dx, dy, dz, __uint_as_float((i << 16) | (pe[r] & 0xFFFFu)));
+                        tail += (uint32_t)__popc(m);
+                        if (tail - head >= 32u) {
+                            ens_batch<SMODE, VIR>(B, S, q, key, head, 32, lane);
+                            head += 32u;
+                        }
                     }
                 }
             }
