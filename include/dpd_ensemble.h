@@ -40,8 +40,9 @@ extern "C" {
 typedef struct dpd_ensemble dpd_ensemble;
 
 typedef struct {
-    int32_t threads;       /* threads per CTA: 128, 256 or 512; 0 = per size class (default 256) */
-    int32_t cluster;       /* CTAs per box: 1, 2, 4 or 8; 0 = per size class (default by box size) */
+    int32_t threads;       /* threads per CTA: 128, 256 or 512; 0 = per size class (512, and 256
+                              for the smallest boxes; fewer when a box's footprint needs it) */
+    int32_t cluster;       /* CTAs per box: 1, 2, 4 or 8; 0 = per size class (2) */
     double wait_timeout_s; /* deadline of every host wait (default 600) */
     void *stream;          /* cudaStream_t; NULL = a stream of the handle */
 } dpd_ensemble_options;

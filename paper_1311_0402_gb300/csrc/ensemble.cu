@@ -140,7 +140,11 @@ int class_of(int64_t n, int ncell, bool lhalf, size_t limit)
     return (int)std::min<size_t>(std::max<size_t>(k, 1), 4) - 1;
 }
 
-int default_cluster(int cls) { return cls == 0 ? 4 : (cls == 1 ? 4 : 2); }
+// Shapes the autotuner chose on seeded streams of boxes of L = 6..10 (512
+// threads and 2 CTAs per box, 256 threads for the smallest class); a launch
+// steps down from these when a box's footprint does not fit.
+int default_threads(int cls) { return cls == 3 ? 256 : 512; }
+int default_cluster(int) { return 2; }
 
 void fill_desc(EnsBox &d, const dpd_box_params *p, int64_t n, const int nc[3])
 {
@@ -275,7 +279,7 @@ dpd_status dpd_ensemble_create(dpd_ensemble **out, const dpd_ensemble_options *o
         return efail(nullptr, DPD_ERR_CUDA, "ensemble setup failed (no GPU, or kernel attributes refused)");
     }
     for (int c = 0; c < kClasses; ++c) {
-        e->threads[c] = o.threads ? o.threads : 256;
+        e->threads[c] = o.threads ? o.threads : default_threads(c);
         e->cluster[c] = o.cluster ? o.cluster : default_cluster(c);
     }
     *out = e;
