@@ -48,3 +48,25 @@ def test_argument_errors_need_no_gpu():
     assert e.value.status == 1
     o = dpd.dpd_default_options()
     assert o.skin == 0.3 and o.seed == 42 and o.lam == 0.5 and o.graph_steps == 8
+
+
+def test_ensemble_fails_loudly_without_a_gpu():
+    dbuild.build()
+    # option validation comes before any CUDA call
+    with pytest.raises(dpd.DPDError) as e:
+        dpd.Ensemble(threads=100)
+    assert e.value.status == 1
+    with pytest.raises(dpd.DPDError) as e:
+        dpd.Ensemble(cluster=3)
+    assert e.value.status == 1
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:
+        # no CPU fallback: creating an ensemble needs the device
+        with pytest.raises(dpd.DPDError) as e:
+            dpd.Ensemble()
+        assert e.value.status == 3
+        assert not dpd.dpd_ensemble_fits((10.0,) * 3, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, 3000)
