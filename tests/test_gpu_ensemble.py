@@ -208,3 +208,66 @@ def test_tuner_picks_a_measured_shape():
     ens.sync()
     assert ens.state(ids[0])[2] == 10
     ens.close()
+
+
+def _largest_fitting_n(box):
+    lo, hi = 1, 65535
+    while lo < hi:  # largest n with fits(n)
+        mid = (lo + hi + 1) // 2
+        if dpd.dpd_ensemble_fits(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, mid):
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+@pytest.mark.parametrize("case", ["non_cubic_three_cells", "largest_fitting_box", "two_species_ragged"])
+def test_edge_boxes_match_oracle(case):
+    """Edge cases of the ensemble kernel against the oracle: a non-cubic box
+    with exactly three cells along x (the smallest stencil without repeated
+    cells), the largest box one CTA's shared memory holds (its launch steps
+    the block size down), and a ragged particle count with two species."""
+    sp, a = None, 25.0
+    if case == "non_cubic_three_cells":
+        box = (3.2, 7.5, 5.1)
+        n = workloads.n_particles(box, 3.0)
+    elif case == "largest_fitting_box":
+        box = (11.0, 11.0, 11.0)
+        n = _largest_fitting_n(box)
+        assert 3993 < n < 65535  # denser than rho = 3
+        assert not dpd.dpd_ensemble_fits(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, n + 1)
+    else:
+        box = (7.3, 6.1, 8.9)
+        n = 1187
+        a = [[25.0, 40.0], [40.0, 30.0]]
+        sp = (np.arange(n) % 3 == 0).astype(np.int32)
+    x, v = workloads.uniform_fluid(box, n, 1.0, 106)[:2]
+    ens = dpd.Ensemble()
+    i = _add(ens, box, x, v, a=a, species=sp, step=4)
+    x32, v32, _ = ens.state(i)
+    o = oracle.System(box, a, 4.5, 1.0, 1.0, 1.0, 0.01, seed=42, cut_fp32=True)
+    fo, vir = o.forces(x32, v32, species=sp, step=4)
+    err, rms = force_error(ens.forces(i), fo)
+    assert err < FORCE_TOL, (case, n, err, rms)
+    assert abs(ens.observables(i)["virial"] - vir) < 1e-5 * abs(vir)
+    ens.step(30)
+    ens.sync()
+    xg, vg, step = ens.state(i)
+    assert step == 34 and np.isfinite(xg).all() and np.isfinite(vg).all()
+    assert (xg >= 0).all() and (xg < np.asarray(box)).all()
+    ens.close()
+
+
+def test_single_particle_box():
+    box = (4.0, 4.0, 4.0)
+    ens = dpd.Ensemble()
+    i = _add(ens, box, np.array([[1.0, 2.0, 3.0]]), np.array([[0.5, -0.25, 0.125]]))
+    assert np.array_equal(ens.forces(i), np.zeros((1, 3)))
+    ens.step(10)
+    ens.sync()
+    x, v, step = ens.state(i)
+    # no force: free flight, wrapped
+    assert step == 10
+    assert np.allclose(v, [[0.5, -0.25, 0.125]], atol=0)
+    assert np.allclose(x, np.mod(np.array([[1.0, 2.0, 3.0]]) + 10 * 0.01 * v, 4.0), atol=1e-5)
+    ens.close()
