@@ -341,28 +341,38 @@ def run_small_boxes(args):
     boxes = workloads.serving_stream(args.small_boxes, seed=workloads.BASE_SEED + 9, L_range=(6, 10),
                                      with_state=True)
     total = float(sum(b["n"] * b["steps"] for b in boxes))
-    ens = dpd.Ensemble()
-    ids = [ens.add(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"], seed=b["seed"])
-           for b in boxes]
-    table = ens.tune(steps=20)
-    ens.sync()
-    threads, cluster = ens.config()
-    left = {i: b["steps"] for i, b in zip(ids, boxes)}
-    done = []
-    t0 = time.perf_counter()
-    while left:
-        ks = list(left)
-        st = [min(100, left[k]) for k in ks]
-        ens.step(st, ids=ks)
+
+    def ensemble_run(newton3):
+        ens = dpd.Ensemble(newton3=newton3)
+        ids = [ens.add(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
+                       seed=b["seed"]) for b in boxes]
+        table = ens.tune(steps=20)
         ens.sync()
-        now = time.perf_counter() - t0
-        for k, c in zip(ks, st):
-            left[k] -= c
-            if left[k] == 0:
-                del left[k]
-                done.append(now)
-    t_ens = time.perf_counter() - t0
-    ens.close()
+        threads, cluster = ens.config()
+        left = {i: b["steps"] for i, b in zip(ids, boxes)}
+        done = []
+        t0 = time.perf_counter()
+        while left:
+            ks = list(left)
+            st = [min(100, left[k]) for k in ks]
+            ens.step(st, ids=ks)
+            ens.sync()
+            now = time.perf_counter() - t0
+            for k, c in zip(ks, st):
+                left[k] -= c
+                if left[k] == 0:
+                    del left[k]
+                    done.append(now)
+        wall = time.perf_counter() - t0
+        ens.close()
+        done = np.array(done)
+        return {"value": total / wall, "unit": UNIT, "wall_s": wall,
+                "p50_s": float(np.percentile(done, 50)), "p99_s": float(np.percentile(done, 99)),
+                "threads_per_cta_by_class": threads, "ctas_per_box_by_class": cluster,
+                "tuner_ms_per_step_last_class": {"%dx%d" % k: v for k, v in table.items()}}
+
+    ens_det = ensemble_run(0)
+    ens_n3 = ensemble_run(1)
     srv = dpd.Server(max_active=args.serve_active, chunk_steps=100)
     t1 = srv.now()
     tickets = [srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"], b["steps"],
@@ -383,15 +393,12 @@ def run_small_boxes(args):
         sim.close()
     t_seq = time.perf_counter() - t2
     seq_total = float(sum(b["n"] * b["steps"] for b in sample))
-    done = np.array(done)
     return {
         "workload": "%d seeded periodic cubes, L uniform in 6..10 (648..3000 particles), rho=3, a in [15,40], "
                     "gamma in [3,6], kT=1, dt=0.01, 500-5000 steps each, all submitted at t=0" % len(boxes),
         "particle_steps": total,
-        "ensemble_kernel": {"value": total / t_ens, "unit": UNIT, "wall_s": t_ens,
-                            "p50_s": float(np.percentile(done, 50)), "p99_s": float(np.percentile(done, 99)),
-                            "threads_per_cta_by_class": threads, "ctas_per_box_by_class": cluster,
-                            "tuner_ms_per_step_last_class": {"%dx%d" % k: v for k, v in table.items()}},
+        "ensemble_kernel": dict(ens_det, mode="every pair from both sides, fixed order (bit-reproducible)"),
+        "ensemble_kernel_newton3": dict(ens_n3, mode="each pair once, partner share by shared-memory atomics"),
         "serving_loop_own_handles": {"value": total / float(tt.max()), "unit": UNIT, "wall_s": float(tt.max()),
                                      "p50_s": float(np.percentile(tt, 50)), "p99_s": float(np.percentile(tt, 99)),
                                      "max_active": args.serve_active},

@@ -17,7 +17,7 @@
  * Results: every force is summed in a fixed order (cells in a fixed stencil
  * order, particles of a cell by index, fixed-size batches), so a box's
  * trajectory is bit-identical whatever the other boxes, the cluster size C and
- * the block size are.  They agree with dpd.h's engine to FP32 rounding, not
+ * the block size are (unless the Newton-3 option is set).  They agree with dpd.h's engine to FP32 rounding, not
  * bit for bit (different summation order).
  *
  * Limits: a box must fit in one CTA's shared memory (about 4,000 particles
@@ -45,6 +45,10 @@ typedef struct {
     int32_t cluster;       /* CTAs per box: 1, 2, 4 or 8; 0 = per size class (2) */
     double wait_timeout_s; /* deadline of every host wait (default 600) */
     void *stream;          /* cudaStream_t; NULL = a stream of the handle */
+    int32_t newton3;       /* 1: each pair evaluated once (half stencil), the partner's share
+                              added by shared-memory atomics, one CTA per box; the last bits
+                              of a trajectory then vary run to run.  0 (default): every pair
+                              from both sides in a fixed order (bit-reproducible). */
 } dpd_ensemble_options;
 
 /* Parameters of one box (the arguments of dpd_create plus the options that

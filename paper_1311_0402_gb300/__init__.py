@@ -155,6 +155,7 @@ class dpd_ensemble_options(ctypes.Structure):
         ("cluster", ctypes.c_int32),
         ("wait_timeout_s", ctypes.c_double),
         ("stream", ctypes.c_void_p),
+        ("newton3", ctypes.c_int32),
     ]
 
 
@@ -677,10 +678,10 @@ class Ensemble:
     (include/dpd_ensemble.h): one thread-block cluster per box, the box
     resident in shared memory for a whole chunk of steps."""
 
-    def __init__(self, threads=0, cluster=0, wait_timeout_s=600.0):
+    def __init__(self, threads=0, cluster=0, wait_timeout_s=600.0, newton3=0):
         o = dpd_ensemble_options()
         lib().dpd_ensemble_default_options(ctypes.byref(o))
-        o.threads, o.cluster, o.wait_timeout_s = threads, cluster, wait_timeout_s
+        o.threads, o.cluster, o.wait_timeout_s, o.newton3 = threads, cluster, wait_timeout_s, newton3
         self.e = ctypes.c_void_p()
         _ens_check(lib().dpd_ensemble_create(ctypes.byref(self.e), ctypes.byref(o)), None)
         self._n = {}

@@ -201,23 +201,24 @@ struct Shape {
     size_t smem;
 };
 
-bool shape_for(const std::vector<const EBox *> &bs, bool lhalf, int s_mode, int threads, int cluster, size_t limit,
-               Shape &out)
+bool shape_for(const std::vector<const EBox *> &bs, bool lhalf, int s_mode, bool n3, int threads, int cluster,
+               size_t limit, Shape &out)
 {
+    if (n3 && cluster != 1) return false;  // Newton-3 mode: one CTA per box
     size_t smem = 0;
     for (const EBox *b : bs) smem = std::max(smem, footprint(b->n, b->desc.ncell, lhalf, threads));
     if (smem > limit) return false;
-    if (ensemble_max_clusters(lhalf, s_mode, threads, cluster, smem) < 1) return false;
+    if (ensemble_max_clusters(lhalf, s_mode, n3, threads, cluster, smem) < 1) return false;
     out = {threads, cluster, smem};
     return true;
 }
 
-bool pick_shape(const std::vector<const EBox *> &bs, bool lhalf, int s_mode, int threads, int cluster, size_t limit,
-                Shape &out)
+bool pick_shape(const std::vector<const EBox *> &bs, bool lhalf, int s_mode, bool n3, int threads, int cluster,
+                size_t limit, Shape &out)
 {
     for (int t = threads; t >= 128; t /= 2)
-        for (int c = cluster; c >= 1; c /= 2)
-            if (shape_for(bs, lhalf, s_mode, t, c, limit, out)) return true;
+        for (int c = n3 ? 1 : cluster; c >= 1; c /= 2)
+            if (shape_for(bs, lhalf, s_mode, n3, t, c, limit, out)) return true;
     return false;
 }
 
@@ -252,6 +253,7 @@ dpd_status dpd_ensemble_create(dpd_ensemble **out, const dpd_ensemble_options *o
     if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8)
         return efail(nullptr, DPD_ERR_ARG, "cluster in {0, 1, 2, 4, 8}");
     if (!(o.wait_timeout_s > 0)) return efail(nullptr, DPD_ERR_ARG, "wait_timeout_s > 0");
+    if (o.newton3 != 0 && o.newton3 != 1) return efail(nullptr, DPD_ERR_ARG, "newton3 in {0, 1}");
     dpd_ensemble *e = new dpd_ensemble();
     e->opt = o;
     if (o.stream) {
@@ -280,7 +282,7 @@ dpd_status dpd_ensemble_create(dpd_ensemble **out, const dpd_ensemble_options *o
     }
     for (int c = 0; c < kClasses; ++c) {
         e->threads[c] = o.threads ? o.threads : default_threads(c);
-        e->cluster[c] = o.cluster ? o.cluster : default_cluster(c);
+        e->cluster[c] = o.newton3 ? 1 : (o.cluster ? o.cluster : default_cluster(c));
     }
     *out = e;
     return DPD_OK;
@@ -472,7 +474,8 @@ dpd_status dpd_ensemble_step(dpd_ensemble *e, const int32_t *ids, const int32_t 
             }
             if (bs.empty()) continue;
             Shape sh;
-            if (!pick_shape(bs, g.lhalf, g.s_mode, e->threads[g.cls], e->cluster[g.cls], e->limit, sh))
+            if (!pick_shape(bs, g.lhalf, g.s_mode, e->opt.newton3 != 0, e->threads[g.cls], e->cluster[g.cls], e->limit,
+                            sh))
                 return efail(e, DPD_ERR_ARG, "no launch shape fits these boxes");
             launches.push_back({g.cls, g.lhalf, g.s_mode, off, (int)bs.size(), sh});
         }
@@ -488,8 +491,8 @@ dpd_status dpd_ensemble_step(dpd_ensemble *e, const int32_t *ids, const int32_t 
             ENS_TRY(e, cudaStreamWaitEvent(s, e->fork, 0));
             used[L.cls] = true;
         }
-        ENS_TRY(e, launch_ensemble(e->d_desc + L.off, L.nb, L.lhalf, L.s_mode, L.shape.threads, L.shape.cluster,
-                                   L.shape.smem, s));
+        ENS_TRY(e, launch_ensemble(e->d_desc + L.off, L.nb, L.lhalf, L.s_mode, e->opt.newton3 != 0, L.shape.threads,
+                                   L.shape.cluster, L.shape.smem, s));
     }
     for (int c = 0; c < kClasses; ++c)
         if (used[c]) {
@@ -702,7 +705,9 @@ dpd_status dpd_ensemble_tune(dpd_ensemble *e, int32_t steps, double *table)
                 bool feasible = true;
                 for (auto &kv : vars) {
                     Shape sh;
-                    if (!shape_for(kv.second, kv.first.first != 0, kv.first.second, T, C, e->limit, sh)) feasible = false;
+                    if (!shape_for(kv.second, kv.first.first != 0, kv.first.second, e->opt.newton3 != 0, T, C, e->limit,
+                                   sh))
+                        feasible = false;
                     shapes.push_back(sh);
                     ++k;
                 }
@@ -725,8 +730,8 @@ dpd_status dpd_ensemble_tune(dpd_ensemble *e, int32_t steps, double *table)
                     size_t v = 0;
                     for (auto &kv : vars) {
                         ENS_TRY(e, launch_ensemble(e->d_desc + spans[v].first, spans[v].second, kv.first.first != 0,
-                                                   kv.first.second, shapes[v].threads, shapes[v].cluster,
-                                                   shapes[v].smem, e->stream));
+                                                   kv.first.second, e->opt.newton3 != 0, shapes[v].threads,
+                                                   shapes[v].cluster, shapes[v].smem, e->stream));
                         ++v;
                     }
                     ENS_TRY(e, cudaEventRecord(e->t1, e->stream));
@@ -760,7 +765,7 @@ dpd_status dpd_ensemble_config(dpd_ensemble *e, int32_t threads[4], int32_t clus
     for (auto &kv : e->boxes) present[kv.second.cls] = true;
     for (int c = 0; c < kClasses; ++c) {
         threads[c] = present[c] ? e->threads[c] : 0;
-        cluster[c] = present[c] ? e->cluster[c] : 0;
+        cluster[c] = present[c] ? (e->opt.newton3 ? 1 : e->cluster[c]) : 0;
     }
     return DPD_OK;
 }

@@ -69,7 +69,9 @@ __host__ __device__ inline EnsLayout ens_layout(int n, int ncell, bool lhalf, in
 
 // Launch the chunk kernel over nb boxes (descriptors in device memory),
 // `cluster` CTAs per box, `threads` per CTA, `smem` dynamic bytes.
-cudaError_t launch_ensemble(const EnsBox *boxes, int nb, bool lhalf, int s_mode, int threads, int cluster,
+// n3: half stencil with shared-memory atomics for the partner's share (one
+// CTA per box: cluster must be 1); otherwise full stencil, fixed order.
+cudaError_t launch_ensemble(const EnsBox *boxes, int nb, bool lhalf, int s_mode, bool n3, int threads, int cluster,
                             size_t smem, cudaStream_t s);
 // Observables of nb boxes: out[8 b + (0..4)] = sum v^2, virial, momentum.
 cudaError_t launch_ensemble_observe(const EnsBox *boxes, int nb, double *out, cudaStream_t s);
@@ -77,6 +79,6 @@ cudaError_t launch_ensemble_observe(const EnsBox *boxes, int nb, double *out, cu
 // the attributes could not be set).
 size_t ensemble_smem_limit();
 // Active clusters of this shape the device can hold at once (0: cannot run).
-int ensemble_max_clusters(bool lhalf, int s_mode, int threads, int cluster, size_t smem);
+int ensemble_max_clusters(bool lhalf, int s_mode, bool n3, int threads, int cluster, size_t smem);
 
 }  // namespace dpd

@@ -116,7 +116,7 @@ __device__ void ens_scan(const uint32_t *cnt, uint32_t *start, int ncell, uint32
 
 // Evaluate ring entries [head, head + nb) (nb <= 32), one pair per lane, and
 // add the sums of each run of equal owners to the owner's accumulator.
-template <int SMODE, bool VIR>
+template <int SMODE, bool VIR, bool N3>
 __device__ __forceinline__ void ens_batch(const EnsBox &B, const EnsPtrs &S, const float4 *q, const uint32_t (&key)[4],
                                           uint32_t head, int nb, int lane)
 {
@@ -150,11 +150,16 @@ __device__ __forceinline__ void ens_batch(const EnsBox &B, const EnsPtrs &S, con
         float a = B.a[0];
         if (B.n_species > 1) a = B.a[__float_as_int(S.pos[i].w) * B.n_species + __float_as_int(S.pos[j].w)];
         const float F = fmaf(a, wgt, fmaf(-B.gamma * wR * wR, ev, B.sigma_isdt * wR * xi));
-        if (VIR) fw = 0.5f * (a * wgt * r);  // each pair is seen from both ends
+        if (VIR) fw = N3 ? a * wgt * r : 0.5f * (a * wgt * r);  // once per pair, or from both ends
         const float sc = -F * inv_r;
         fx = sc * dx;
         fy = sc * dy;
         fz = sc * dz;
+        if (N3) {  // Newton's third law: the partner gets -F e_ij
+            atomicAdd(&S.f[j].x, -fx);
+            atomicAdd(&S.f[j].y, -fy);
+            atomicAdd(&S.f[j].z, -fz);
+        }
     }
     // segmented inclusive scan over runs of equal owners (fixed order)
     const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, owner, 1);
@@ -176,18 +181,27 @@ __device__ __forceinline__ void ens_batch(const EnsBox &B, const EnsPtrs &S, con
     }
     const uint32_t next = __shfl_down_sync(0xFFFFFFFFu, owner, 1);
     if (lane < nb && (lane == 31 || next != owner)) {
-        float4 acc = S.f[owner];
-        acc.x += fx;
-        acc.y += fy;
-        acc.z += fz;
-        if (VIR) acc.w += fw;
-        S.f[owner] = acc;
+        if (N3) {  // other warps add partner shares to the same accumulator
+            atomicAdd(&S.f[owner].x, fx);
+            atomicAdd(&S.f[owner].y, fy);
+            atomicAdd(&S.f[owner].z, fz);
+            if (VIR) atomicAdd(&S.f[owner].w, fw);
+        } else {
+            float4 acc = S.f[owner];
+            acc.x += fx;
+            acc.y += fy;
+            acc.z += fz;
+            if (VIR) acc.w += fw;
+            S.f[owner] = acc;
+        }
     }
     __syncwarp();
 }
 
 // Pair forces of the owners in work unit u (cells [u K, u K + K)) into S.f.
-template <int SMODE, bool VIR>
+// N3: half stencil (the own cell's later members and the 13 forward cells),
+// the partner's share added by a shared-memory atomic.
+template <int SMODE, bool VIR, bool N3>
 __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t *cand, int u, int lane)
 {
     const uint32_t key[4] = {B.key[0], B.key[1], B.key[2], B.key[3]};
@@ -198,14 +212,22 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
     for (int c = c0; c < c1; ++c) {
         const int ob = (int)S.start[c], oe = (int)S.start[c + 1];
         if (ob == oe) continue;
-        for (int k = ob + lane; k < oe; k += 32) S.f[S.idx[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!N3)
+            for (int k = ob + lane; k < oe; k += 32) S.f[S.idx[k]] = make_float4(0.f, 0.f, 0.f, 0.f);
         // lane l < 27: neighbour cell l of the stencil, its member range and shift
         const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
         // (the shift stays in the lane's registers; a candidate fetches it by shuffle)
         int len = 0, sbeg = 0;
         float shx = 0.f, shy = 0.f, shz = 0.f;
-        if (lane < 27) {
-            int x = cx + lane % 3 - 1, y = cy + (lane / 3) % 3 - 1, z = cz + lane / 9 - 1;
+        if (lane < (N3 ? 14 : 27)) {
+            int ox = lane % 3 - 1, oy = (lane / 3) % 3 - 1, oz = lane / 9 - 1;
+            if (N3) {  // lane 0: the own cell; lanes 1..13: the forward offsets
+                const int k = lane - 1;
+                ox = lane == 0 ? 0 : (k < 9 ? k % 3 - 1 : (k < 12 ? k - 10 : 1));
+                oy = lane == 0 ? 0 : (k < 9 ? k / 3 - 1 : (k < 12 ? 1 : 0));
+                oz = lane == 0 ? 0 : (k < 9 ? 1 : 0);
+            }
+            int x = cx + ox, y = cy + oy, z = cz + oz;
             if (x < 0) { x += ncx; shx = -B.L[0]; } else if (x >= ncx) { x -= ncx; shx = B.L[0]; }
             if (y < 0) { y += ncy; shy = -B.L[1]; } else if (y >= ncy) { y -= ncy; shy = B.L[1]; }
             if (z < 0) { z += ncz; shz = -B.L[2]; } else if (z >= ncz) { z -= ncz; shz = B.L[2]; }
@@ -221,9 +243,10 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
         }
         const int pre = incl - len;
         const int ncand = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const int len0 = __shfl_sync(0xFFFFFFFFu, len, 0);  // N3: the own cell leads the candidates
         for (int base = 0; base < ncand; base += kEnsCand) {
             __syncwarp();
-            if (lane < 27) {
+            if (lane < (N3 ? 14 : 27)) {
                 const int lo = max(pre, base), hi = min(pre + len, base + kEnsCand);
                 for (int p = lo; p < hi; ++p) cand[p - base] = (uint32_t)S.idx[sbeg + p - pre] | ((uint32_t)lane << 16);
             }
@@ -274,14 +297,17 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
                             dz = __fadd_rn(dz, __shfl_sync(0xFFFFFFFFu, shz, sl));
                         }
                         const float d2 = dist2_rn(dx, dy, dz);
-                        const bool hit = (d2 < B.rc2) & (d2 > 0.0f);
+                        // N3: of the own cell only the members after the owner
+                        const int tg = base + 32 * r + lane;
+                        const bool fwd = !N3 || tg >= len0 || tg > o - ob;
+                        const bool hit = (d2 < B.rc2) & (d2 > 0.0f) & fwd;
                         const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
                         if (hit)
                             q[(tail + __popc(m & lt)) & (kEnsQueue - 1)] =
                                 make_float4(dx, dy, dz, __uint_as_float((i << 16) | (pe[r] & 0xFFFFu)));
                         tail += (uint32_t)__popc(m);
                         if (tail - head >= 32u) {
-                            ens_batch<SMODE, VIR>(B, S, q, key, head, 32, lane);
+                            ens_batch<SMODE, VIR, N3>(B, S, q, key, head, 32, lane);
                             head += 32u;
                         }
                     }
@@ -292,7 +318,7 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
             if (base + kEnsCand < ncand) {
                 while (tail != head) {
                     const int nb = (int)min(32u, tail - head);
-                    ens_batch<SMODE, VIR>(B, S, q, key, head, nb, lane);
+                    ens_batch<SMODE, VIR, N3>(B, S, q, key, head, nb, lane);
                     head += (uint32_t)nb;
                 }
             }
@@ -300,12 +326,12 @@ __device__ void ens_unit(const EnsBox &B, const EnsPtrs &S, float4 *q, uint32_t 
     }
     while (tail != head) {
         const int nb = (int)min(32u, tail - head);
-        ens_batch<SMODE, VIR>(B, S, q, key, head, nb, lane);
+        ens_batch<SMODE, VIR, N3>(B, S, q, key, head, nb, lane);
         head += (uint32_t)nb;
     }
 }
 
-template <bool LHALF, int SMODE>
+template <bool LHALF, int SMODE, bool N3>
 __global__ void __launch_bounds__(kEnsMaxThreads, 1) k_ens_run(const EnsBox *__restrict__ boxes, int C)
 {
     __shared__ EnsBox B;
@@ -375,7 +401,10 @@ __global__ void __launch_bounds__(kEnsMaxThreads, 1) k_ens_run(const EnsBox *__r
         for (int i = threadIdx.x; i < n; i += T) S.slot[i] = (uint16_t)atomicAdd(&S.cnt[ens_cell(B, S.pos[i])], 1u);
         __syncthreads();
         ens_scan(S.cnt, S.start, ncell, wsum);
-        for (int i = threadIdx.x; i < n; i += T) S.idx[S.start[ens_cell(B, S.pos[i])] + S.slot[i]] = (uint16_t)i;
+        for (int i = threadIdx.x; i < n; i += T) {
+            S.idx[S.start[ens_cell(B, S.pos[i])] + S.slot[i]] = (uint16_t)i;
+            if (N3) S.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // partner shares may come from any warp
+        }
         for (int c = threadIdx.x; c < ncell; c += T) S.cnt[c] = 0u;
         __syncthreads();
         for (int c = threadIdx.x; c < ncell; c += T) {  // members of a cell in index order
@@ -393,8 +422,8 @@ __global__ void __launch_bounds__(kEnsMaxThreads, 1) k_ens_run(const EnsBox *__r
         __syncthreads();
         // 2. pair forces of this CTA's units
         for (int u = rank + C * warp; u < nunits; u += C * nwarps) {
-            if (last) ens_unit<SMODE, true>(B, S, q, cand, u, lane);
-            else ens_unit<SMODE, false>(B, S, q, cand, u, lane);
+            if (last) ens_unit<SMODE, true, N3>(B, S, q, cand, u, lane);
+            else ens_unit<SMODE, false, N3>(B, S, q, cand, u, lane);
         }
         __syncthreads();
         if (C > 1) cl.sync();  // every replica has been read for this step
@@ -501,15 +530,18 @@ __global__ void __launch_bounds__(kObsThreads) k_ens_observe(const EnsBox *__res
 
 using EnsKernel = void (*)(const EnsBox *, int);
 
-EnsKernel pick(bool lhalf, int s_mode)
+template <bool N3>
+EnsKernel pick_n3(bool lhalf, int s_mode)
 {
     switch (s_mode) {
-    case 1: return lhalf ? k_ens_run<true, 1> : k_ens_run<false, 1>;
-    case 2: return lhalf ? k_ens_run<true, 2> : k_ens_run<false, 2>;
-    case 3: return lhalf ? k_ens_run<true, 3> : k_ens_run<false, 3>;
-    default: return lhalf ? k_ens_run<true, 0> : k_ens_run<false, 0>;
+    case 1: return lhalf ? k_ens_run<true, 1, N3> : k_ens_run<false, 1, N3>;
+    case 2: return lhalf ? k_ens_run<true, 2, N3> : k_ens_run<false, 2, N3>;
+    case 3: return lhalf ? k_ens_run<true, 3, N3> : k_ens_run<false, 3, N3>;
+    default: return lhalf ? k_ens_run<true, 0, N3> : k_ens_run<false, 0, N3>;
     }
 }
+
+EnsKernel pick(bool lhalf, int s_mode, bool n3) { return n3 ? pick_n3<true>(lhalf, s_mode) : pick_n3<false>(lhalf, s_mode); }
 
 size_t g_limit = 0;
 std::once_flag g_once;
@@ -523,22 +555,20 @@ void init_attributes()
         return;
     }
     size_t limit = (size_t)optin;
-    for (int l = 0; l < 2; ++l)
-        for (int m = 0; m < 4; ++m) {
-            cudaFuncAttributes fa;
-            if (cudaFuncGetAttributes(&fa, pick(l == 1, m)) != cudaSuccess) {
-                cudaGetLastError();
-                return;
-            }
-            limit = std::min(limit, (size_t)optin - fa.sharedSizeBytes);
+    for (int v = 0; v < 16; ++v) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, pick(v & 1, (v >> 1) & 3, v >> 3)) != cudaSuccess) {
+            cudaGetLastError();
+            return;
         }
-    for (int l = 0; l < 2; ++l)
-        for (int m = 0; m < 4; ++m)
-            if (cudaFuncSetAttribute(pick(l == 1, m), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) !=
-                cudaSuccess) {
-                cudaGetLastError();
-                return;
-            }
+        limit = std::min(limit, (size_t)optin - fa.sharedSizeBytes);
+    }
+    for (int v = 0; v < 16; ++v)
+        if (cudaFuncSetAttribute(pick(v & 1, (v >> 1) & 3, v >> 3), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)limit) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
     g_limit = limit;
 }
 
@@ -566,29 +596,30 @@ size_t ensemble_smem_limit()
     return g_limit;
 }
 
-int ensemble_max_clusters(bool lhalf, int s_mode, int threads, int cluster, size_t smem)
+int ensemble_max_clusters(bool lhalf, int s_mode, bool n3, int threads, int cluster, size_t smem)
 {
     if (ensemble_smem_limit() == 0 || smem > g_limit) return 0;
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = config_for(cluster, threads, cluster, smem, nullptr, at);
     int num = 0;
-    if (cudaOccupancyMaxActiveClusters(&num, pick(lhalf, s_mode), &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&num, pick(lhalf, s_mode, n3), &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return num;
 }
 
-cudaError_t launch_ensemble(const EnsBox *boxes, int nb, bool lhalf, int s_mode, int threads, int cluster,
+cudaError_t launch_ensemble(const EnsBox *boxes, int nb, bool lhalf, int s_mode, bool n3, int threads, int cluster,
                             size_t smem, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
+    // Newton-3 mode keeps every partner in the CTA's own shared memory: one CTA per box
     if (ensemble_smem_limit() == 0 || smem > g_limit || threads < 32 || threads > kEnsMaxThreads ||
-        threads % 32 != 0 || cluster < 1 || cluster > kEnsMaxCluster)
+        threads % 32 != 0 || cluster < 1 || cluster > kEnsMaxCluster || (n3 && cluster != 1))
         return cudaErrorInvalidValue;
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = config_for(nb, threads, cluster, smem, s, at);
-    return cudaLaunchKernelEx(&cfg, pick(lhalf, s_mode), boxes, cluster);
+    return cudaLaunchKernelEx(&cfg, pick(lhalf, s_mode, n3), boxes, cluster);
 }
 
 cudaError_t launch_ensemble_observe(const EnsBox *boxes, int nb, double *out, cudaStream_t s)

@@ -271,3 +271,64 @@ def test_single_particle_box():
     assert np.allclose(v, [[0.5, -0.25, 0.125]], atol=0)
     assert np.allclose(x, np.mod(np.array([[1.0, 2.0, 3.0]]) + 10 * 0.01 * v, 4.0), atol=1e-5)
     ens.close()
+
+
+@pytest.mark.parametrize("case", ["one_species", "s_quarter", "non_cubic_three_cells", "two_species"])
+def test_newton3_forces_match_oracle(case):
+    """Newton-3 mode (half stencil, partner shares by shared-memory atomics):
+    the same forces within 1e-4 of the RMS force."""
+    box, x, v = _fluid(8, 107)
+    a, s, sp = 25.0, 1.0, None
+    if case == "s_quarter":
+        s = 0.25
+    elif case == "non_cubic_three_cells":
+        box = (3.2, 7.5, 5.1)
+        x, v = workloads.uniform_fluid(box, workloads.n_particles(box, 3.0), 1.0, 108)[:2]
+    elif case == "two_species":
+        a = [[25.0, 60.0], [60.0, 25.0]]
+        sp = (np.arange(x.shape[0]) % 2).astype(np.int32)
+    ens = dpd.Ensemble(newton3=1, cluster=4)  # one CTA per box whatever is asked
+    i = _add(ens, box, x, v, a=a, s=s, species=sp, step=6)
+    x32, v32, _ = ens.state(i)
+    o = oracle.System(box, a, 4.5, 1.0, 1.0, s, 0.01, seed=42, cut_fp32=True)
+    fo, vir = o.forces(x32, v32, species=sp, step=6)
+    err, rms = force_error(ens.forces(i), fo)
+    assert err < FORCE_TOL, (case, err, rms)
+    assert abs(ens.observables(i)["virial"] - vir) < 1e-5 * abs(vir)
+    assert all(c in (0, 1) for c in ens.config()[1])
+    ens.close()
+
+
+def test_newton3_trajectory_and_thermodynamics():
+    box, x, v = _fluid(9, 109)
+    ens = dpd.Ensemble(newton3=1)
+    i = _add(ens, box, x, v, step=3)
+    x32, v32, _ = ens.state(i)
+    o = oracle.System(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, seed=42, cut_fp32=True)
+    f0, _ = o.forces(x32, v32, step=3)
+    res = o.run(x32, v32, 2, step=3, f=f0)
+    ens.step(2)
+    ens.sync()
+    xg, vg, _ = ens.state(i)
+    dx = xg - res["x"]
+    dx -= np.asarray(box) * np.round(dx / np.asarray(box))
+    assert np.abs(dx).max() < 1e-5 and np.abs(vg - res["v"]).max() < 1e-3
+    # long run against the deterministic mode (independent rounding, same physics)
+    det = dpd.Ensemble()
+    j = _add(det, box, x, v, seed=43)
+    ens.step(500)
+    det.step(500)
+    t3, p3, td, pd = [], [], [], []
+    for _ in range(50):
+        ens.step(20)
+        det.step(20)
+        ens.sync()
+        det.sync()
+        a, b = ens.observables(i), det.observables(j)
+        t3.append(a["temperature"]); p3.append(a["pressure"])
+        td.append(b["temperature"]); pd.append(b["pressure"])
+    assert abs(np.mean(t3) - np.mean(td)) < 0.015
+    assert abs(np.mean(p3) - np.mean(pd)) < 0.01 * np.mean(pd)
+    assert abs(ens.observables(i)["momentum"]).max() < 1e-2
+    ens.close()
+    det.close()
