@@ -46,9 +46,10 @@ typedef struct {
     double wait_timeout_s; /* deadline of every host wait (default 600) */
     void *stream;          /* cudaStream_t; NULL = a stream of the handle */
     int32_t newton3;       /* 1: each pair evaluated once (half stencil), the partner's share
-                              added by shared-memory atomics, one CTA per box; the last bits
-                              of a trajectory then vary run to run.  0 (default): every pair
-                              from both sides in a fixed order (bit-reproducible). */
+                              added by an atomic in the shared memory of the CTA that owns
+                              it; the last bits of a trajectory then vary run to run.
+                              0 (default): every pair from both sides in a fixed order
+                              (bit-reproducible). */
 } dpd_ensemble_options;
 
 /* Parameters of one box (the arguments of dpd_create plus the options that

@@ -204,7 +204,6 @@ struct Shape {
 bool shape_for(const std::vector<const EBox *> &bs, bool lhalf, int s_mode, bool n3, int threads, int cluster,
                size_t limit, Shape &out)
 {
-    if (n3 && cluster != 1) return false;  // Newton-3 mode: one CTA per box
     size_t smem = 0;
     for (const EBox *b : bs) smem = std::max(smem, footprint(b->n, b->desc.ncell, lhalf, threads));
     if (smem > limit) return false;
@@ -217,7 +216,7 @@ bool pick_shape(const std::vector<const EBox *> &bs, bool lhalf, int s_mode, boo
                 size_t limit, Shape &out)
 {
     for (int t = threads; t >= 128; t /= 2)
-        for (int c = n3 ? 1 : cluster; c >= 1; c /= 2)
+        for (int c = cluster; c >= 1; c /= 2)
             if (shape_for(bs, lhalf, s_mode, n3, t, c, limit, out)) return true;
     return false;
 }
@@ -282,7 +281,7 @@ dpd_status dpd_ensemble_create(dpd_ensemble **out, const dpd_ensemble_options *o
     }
     for (int c = 0; c < kClasses; ++c) {
         e->threads[c] = o.threads ? o.threads : default_threads(c);
-        e->cluster[c] = o.newton3 ? 1 : (o.cluster ? o.cluster : default_cluster(c));
+        e->cluster[c] = o.cluster ? o.cluster : default_cluster(c);
     }
     *out = e;
     return DPD_OK;
@@ -765,7 +764,7 @@ dpd_status dpd_ensemble_config(dpd_ensemble *e, int32_t threads[4], int32_t clus
     for (auto &kv : e->boxes) present[kv.second.cls] = true;
     for (int c = 0; c < kClasses; ++c) {
         threads[c] = present[c] ? e->threads[c] : 0;
-        cluster[c] = present[c] ? (e->opt.newton3 ? 1 : e->cluster[c]) : 0;
+        cluster[c] = present[c] ? e->cluster[c] : 0;
     }
     return DPD_OK;
 }

@@ -43,9 +43,10 @@ __host__ __device__ inline size_t ens_align16(size_t b) { return (b + 15) & ~siz
 // Dynamic shared memory of one CTA, in this order: pos, u (the velocity the
 // pair force reads, + signature), vh (lambda != 1/2 only), f, cell starts
 // [ncell + 1], cell counts [ncell], sorted indices [n], arrival slots [n],
-// then per warp the hit ring and the candidate buffer.
+// owning CTA of each particle this step [n] (Newton-3 mode), then per warp
+// the hit ring and the candidate buffer.
 struct EnsLayout {
-    size_t pos, u, vh, f, start, cnt, idx, slot, q, cand, total;
+    size_t pos, u, vh, f, start, cnt, idx, slot, own, q, cand, total;
 };
 
 __host__ __device__ inline EnsLayout ens_layout(int n, int ncell, bool lhalf, int threads)
@@ -60,6 +61,7 @@ __host__ __device__ inline EnsLayout ens_layout(int n, int ncell, bool lhalf, in
     l.cnt = o; o += ens_align16((size_t)ncell * 4);
     l.idx = o; o += ens_align16((size_t)n * 2);
     l.slot = o; o += ens_align16((size_t)n * 2);
+    l.own = o; o += ens_align16((size_t)n);
     const int warps = threads / 32;
     l.q = o; o += (size_t)warps * kEnsQueue * 16;
     l.cand = o; o += (size_t)warps * kEnsCand * 4;
@@ -69,8 +71,8 @@ __host__ __device__ inline EnsLayout ens_layout(int n, int ncell, bool lhalf, in
 
 // Launch the chunk kernel over nb boxes (descriptors in device memory),
 // `cluster` CTAs per box, `threads` per CTA, `smem` dynamic bytes.
-// n3: half stencil with shared-memory atomics for the partner's share (one
-// CTA per box: cluster must be 1); otherwise full stencil, fixed order.
+// n3: half stencil, the partner's share added by an atomic to the shared
+// memory of the CTA that owns it; otherwise full stencil, fixed order.
 cudaError_t launch_ensemble(const EnsBox *boxes, int nb, bool lhalf, int s_mode, bool n3, int threads, int cluster,
                             size_t smem, cudaStream_t s);
 // Observables of nb boxes: out[8 b + (0..4)] = sum v^2, virial, momentum.

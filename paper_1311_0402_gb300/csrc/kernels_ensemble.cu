@@ -23,6 +23,9 @@
 //      Within a candidate round every owner's hits are one run of the ring;
 //      the ring is emptied between rounds, so a batch never holds two runs of
 //      one owner;
+//      In the optional Newton-3 mode the stencil is halved (the own cell's
+//      later members and the 13 forward cells) and the partner's share goes
+//      by an atomic to the shared memory of the CTA that integrates it;
 //   3. integrates the particles of its cells (the lambda form of velocity
 //      Verlet, Sec. 3.1 / Algorithm 1) and stores their new state into every
 //      replica of the cluster through distributed shared memory.
@@ -75,6 +78,8 @@ struct EnsPtrs {
     float4 *pos, *u, *vh, *f;
     uint32_t *start, *cnt;
     uint16_t *idx, *slot;
+    uint8_t *own;  // Newton-3 mode: the cluster rank that integrates each particle this step
+    int C, rank;   // CTAs per box, this CTA's rank
 };
 
 // Exclusive scan of cnt[0, ncell) into start[0, ncell], start[ncell] = total.
@@ -155,10 +160,12 @@ __device__ __forceinline__ void ens_batch(const EnsBox &B, const EnsPtrs &S, con
         fx = sc * dx;
         fy = sc * dy;
         fz = sc * dz;
-        if (N3) {  // Newton's third law: the partner gets -F e_ij
-            atomicAdd(&S.f[j].x, -fx);
-            atomicAdd(&S.f[j].y, -fy);
-            atomicAdd(&S.f[j].z, -fz);
+        if (N3) {  // Newton's third law: the partner gets -F e_ij, in its owner's shared memory
+            float4 *fj = S.f;
+            if (S.C > 1 && (int)S.own[j] != S.rank) fj = cg::this_cluster().map_shared_rank(S.f, (int)S.own[j]);
+            atomicAdd(&fj[j].x, -fx);
+            atomicAdd(&fj[j].y, -fy);
+            atomicAdd(&fj[j].z, -fz);
         }
     }
     // segmented inclusive scan over runs of equal owners (fixed order)
@@ -358,6 +365,9 @@ __global__ void __launch_bounds__(kEnsMaxThreads, 1) k_ens_run(const EnsBox *__r
     S.cnt = reinterpret_cast<uint32_t *>(smem + lay.cnt);
     S.idx = reinterpret_cast<uint16_t *>(smem + lay.idx);
     S.slot = reinterpret_cast<uint16_t *>(smem + lay.slot);
+    S.own = reinterpret_cast<uint8_t *>(smem + lay.own);
+    S.C = C;
+    S.rank = rank;
     float4 *q = reinterpret_cast<float4 *>(smem + lay.q) + warp * kEnsQueue;
     uint32_t *cand = reinterpret_cast<uint32_t *>(smem + lay.cand) + warp * kEnsCand;
     const int steps = B.steps;
@@ -402,8 +412,12 @@ __global__ void __launch_bounds__(kEnsMaxThreads, 1) k_ens_run(const EnsBox *__r
         __syncthreads();
         ens_scan(S.cnt, S.start, ncell, wsum);
         for (int i = threadIdx.x; i < n; i += T) {
-            S.idx[S.start[ens_cell(B, S.pos[i])] + S.slot[i]] = (uint16_t)i;
-            if (N3) S.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);  // partner shares may come from any warp
+            const int c = ens_cell(B, S.pos[i]);
+            S.idx[S.start[c] + S.slot[i]] = (uint16_t)i;
+            if (N3) {  // partner shares may come from any warp of the cluster
+                S.f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                S.own[i] = (uint8_t)((c / kEnsUnitCells) % C);
+            }
         }
         for (int c = threadIdx.x; c < ncell; c += T) S.cnt[c] = 0u;
         __syncthreads();
@@ -420,6 +434,7 @@ __global__ void __launch_bounds__(kEnsMaxThreads, 1) k_ens_run(const EnsBox *__r
             }
         }
         __syncthreads();
+        if (N3 && C > 1) cl.sync();  // every replica's accumulators are zero before any remote add
         // 2. pair forces of this CTA's units
         for (int u = rank + C * warp; u < nunits; u += C * nwarps) {
             if (last) ens_unit<SMODE, true, N3>(B, S, q, cand, u, lane);
@@ -613,9 +628,8 @@ cudaError_t launch_ensemble(const EnsBox *boxes, int nb, bool lhalf, int s_mode,
                             size_t smem, cudaStream_t s)
 {
     if (nb <= 0) return cudaSuccess;
-    // Newton-3 mode keeps every partner in the CTA's own shared memory: one CTA per box
     if (ensemble_smem_limit() == 0 || smem > g_limit || threads < 32 || threads > kEnsMaxThreads ||
-        threads % 32 != 0 || cluster < 1 || cluster > kEnsMaxCluster || (n3 && cluster != 1))
+        threads % 32 != 0 || cluster < 1 || cluster > kEnsMaxCluster)
         return cudaErrorInvalidValue;
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = config_for(nb, threads, cluster, smem, s, at);

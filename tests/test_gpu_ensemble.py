@@ -273,10 +273,12 @@ def test_single_particle_box():
     ens.close()
 
 
+@pytest.mark.parametrize("cluster", [1, 4])
 @pytest.mark.parametrize("case", ["one_species", "s_quarter", "non_cubic_three_cells", "two_species"])
-def test_newton3_forces_match_oracle(case):
-    """Newton-3 mode (half stencil, partner shares by shared-memory atomics):
-    the same forces within 1e-4 of the RMS force."""
+def test_newton3_forces_match_oracle(case, cluster):
+    """Newton-3 mode (half stencil, the partner's share added by an atomic in
+    the shared memory of the CTA that owns it, across the cluster with 4 CTAs
+    per box): the same forces within 1e-4 of the RMS force."""
     box, x, v = _fluid(8, 107)
     a, s, sp = 25.0, 1.0, None
     if case == "s_quarter":
@@ -287,7 +289,7 @@ def test_newton3_forces_match_oracle(case):
     elif case == "two_species":
         a = [[25.0, 60.0], [60.0, 25.0]]
         sp = (np.arange(x.shape[0]) % 2).astype(np.int32)
-    ens = dpd.Ensemble(newton3=1, cluster=4)  # one CTA per box whatever is asked
+    ens = dpd.Ensemble(newton3=1, cluster=cluster)
     i = _add(ens, box, x, v, a=a, s=s, species=sp, step=6)
     x32, v32, _ = ens.state(i)
     o = oracle.System(box, a, 4.5, 1.0, 1.0, s, 0.01, seed=42, cut_fp32=True)
@@ -295,13 +297,12 @@ def test_newton3_forces_match_oracle(case):
     err, rms = force_error(ens.forces(i), fo)
     assert err < FORCE_TOL, (case, err, rms)
     assert abs(ens.observables(i)["virial"] - vir) < 1e-5 * abs(vir)
-    assert all(c in (0, 1) for c in ens.config()[1])
     ens.close()
 
 
 def test_newton3_trajectory_and_thermodynamics():
     box, x, v = _fluid(9, 109)
-    ens = dpd.Ensemble(newton3=1)
+    ens = dpd.Ensemble(newton3=1, cluster=2)
     i = _add(ens, box, x, v, step=3)
     x32, v32, _ = ens.state(i)
     o = oracle.System(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, seed=42, cut_fp32=True)
