@@ -680,7 +680,17 @@ dpd_status dpd_ensemble_tune(dpd_ensemble *e, int32_t steps, double *table)
         }
         auto release = [&]() {
             for (void *p : scratch) cudaFreeAsync(p, e->stream);
+            scratch.clear();
         };
+        // a CUDA failure inside the timing loop: scratch back to the pool, then report
+#define TUNE_TRY(call)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            release();                                                                                 \
+            return efail(e, DPD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+        }                                                                                              \
+    } while (0)
         if (!ok) {
             release();
             return efail(e, DPD_ERR_OOM, "tuner scratch allocation failed");
@@ -690,7 +700,7 @@ dpd_status dpd_ensemble_tune(dpd_ensemble *e, int32_t steps, double *table)
             release();
             return st;
         }
-        ENS_TRY(e, cudaMemcpyAsync(e->d_desc, descs.data(), descs.size() * sizeof(EnsBox), cudaMemcpyHostToDevice,
+        TUNE_TRY(cudaMemcpyAsync(e->d_desc, descs.data(), descs.size() * sizeof(EnsBox), cudaMemcpyHostToDevice,
                                    e->stream));
         double best = std::numeric_limits<double>::infinity();
         int best_t = e->threads[cls], best_c = e->cluster[cls];
@@ -718,28 +728,28 @@ dpd_status dpd_ensemble_tune(dpd_ensemble *e, int32_t steps, double *table)
                     for (auto &kv : vars)
                         for (const EBox *b : kv.second) {
                             const size_t f4 = ens_align16((size_t)b->n * 16);
-                            ENS_TRY(e, cudaMemcpyAsync(scratch[j], b->desc.pos, f4, cudaMemcpyDeviceToDevice, e->stream));
-                            ENS_TRY(e, cudaMemcpyAsync((char *)scratch[j] + f4, b->desc.vel, f4, cudaMemcpyDeviceToDevice,
+                            TUNE_TRY(cudaMemcpyAsync(scratch[j], b->desc.pos, f4, cudaMemcpyDeviceToDevice, e->stream));
+                            TUNE_TRY(cudaMemcpyAsync((char *)scratch[j] + f4, b->desc.vel, f4, cudaMemcpyDeviceToDevice,
                                                        e->stream));
-                            ENS_TRY(e, cudaMemcpyAsync((char *)scratch[j] + 2 * f4, b->desc.frc, f4,
+                            TUNE_TRY(cudaMemcpyAsync((char *)scratch[j] + 2 * f4, b->desc.frc, f4,
                                                        cudaMemcpyDeviceToDevice, e->stream));
                             ++j;
                         }
-                    ENS_TRY(e, cudaEventRecord(e->t0, e->stream));
+                    TUNE_TRY(cudaEventRecord(e->t0, e->stream));
                     size_t v = 0;
                     for (auto &kv : vars) {
-                        ENS_TRY(e, launch_ensemble(e->d_desc + spans[v].first, spans[v].second, kv.first.first != 0,
+                        TUNE_TRY(launch_ensemble(e->d_desc + spans[v].first, spans[v].second, kv.first.first != 0,
                                                    kv.first.second, e->opt.newton3 != 0, shapes[v].threads,
                                                    shapes[v].cluster, shapes[v].smem, e->stream));
                         ++v;
                     }
-                    ENS_TRY(e, cudaEventRecord(e->t1, e->stream));
+                    TUNE_TRY(cudaEventRecord(e->t1, e->stream));
                     st = ewait(e);
                     if (st) {
                         release();
                         return st;
                     }
-                    ENS_TRY(e, cudaEventElapsedTime(&ms, e->t0, e->t1));
+                    TUNE_TRY(cudaEventElapsedTime(&ms, e->t0, e->t1));
                 }
                 tab[ti * 4 + ci] = (double)ms / steps;
                 if (tab[ti * 4 + ci] < best) {
@@ -749,6 +759,7 @@ dpd_status dpd_ensemble_tune(dpd_ensemble *e, int32_t steps, double *table)
                 }
             }
         release();
+#undef TUNE_TRY
         if (table) std::memcpy(table, tab, sizeof(tab));
         e->threads[cls] = best_t;
         e->cluster[cls] = best_c;
@@ -772,6 +783,10 @@ dpd_status dpd_ensemble_config(dpd_ensemble *e, int32_t threads[4], int32_t clus
 void dpd_ensemble_destroy(dpd_ensemble *e)
 {
     if (!e) return;
+    // a step that failed after forking may have left launches on the class
+    // streams that the handle's stream never joined: let them finish first
+    for (int c = 0; c < kClasses; ++c)
+        if (e->cls_stream[c]) cudaStreamSynchronize(e->cls_stream[c]);
     if (e->stream) {
         for (auto &kv : e->boxes) cudaFreeAsync(kv.second.mem, e->stream);
         if (e->d_desc) cudaFreeAsync(e->d_desc, e->stream);
