@@ -22,20 +22,23 @@
 //      seen from both sides).
 //      Within a candidate round every owner's hits are one run of the ring;
 //      the ring is emptied between rounds, so a batch never holds two runs of
-//      one owner;
-//      In the optional Newton-3 mode the stencil is halved (the own cell's
-//      later members and the 13 forward cells) and the partner's share goes
-//      by an atomic to the shared memory of the CTA that integrates it;
+//      one owner.  In the optional Newton-3 mode the stencil is halved (the
+//      own cell's later members and the 13 forward cells) and the partner's
+//      share goes by an atomic to the shared memory of the CTA that
+//      integrates it;
 //   3. integrates the particles of its cells (the lambda form of velocity
 //      Verlet, Sec. 3.1 / Algorithm 1) and stores their new state into every
 //      replica of the cluster through distributed shared memory.
 // Two cluster barriers per step separate the reads of a step from the
-// writes of the next.  The last step writes positions, full-step velocities
-// and forces (w = the particle's virial share) to device memory.
+// writes of the next (a third, in Newton-3 mode with more than one CTA per
+// box, orders the zeroing of every replica's accumulators before any remote
+// add).  The last step writes positions, full-step velocities and forces
+// (w = the particle's virial share) to device memory.
 //
-// Fixed summation order: units never span a queue flush, a cell's members are
-// in index order and the stencil order is fixed, so a force does not depend on
-// the cluster size, the block size or the other boxes of the launch.
+// Fixed summation order (the default mode): units never span a queue flush, a
+// cell's members are in index order and the stencil order is fixed, so a force
+// does not depend on the cluster size, the block size or the other boxes of
+// the launch.
 #include "dpd_math.cuh"
 #include "ensemble.cuh"
 
