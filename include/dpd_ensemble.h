@@ -11,14 +11,15 @@
  * cells of side >= r_c (the cell list of Sec. 3.2.3), evaluates the pair
  * forces of its share of the cells (the 27-cell stencil of Sec. 3.3.1, no
  * neighbour list, no skin), integrates the particles it owns and sends their
- * new state to the other replicas through distributed shared memory.  Nothing goes to device memory between the
- * chunk's first and last step.
+ * new state to the other replicas through distributed shared memory.
+ * Nothing goes to device memory between the chunk's first and last step.
  *
  * Results: every force is summed in a fixed order (cells in a fixed stencil
  * order, particles of a cell by index, fixed-size batches), so a box's
- * trajectory is bit-identical whatever the other boxes, the cluster size C and
- * the block size are (unless the Newton-3 option is set).  They agree with dpd.h's engine to FP32 rounding, not
- * bit for bit (different summation order).
+ * trajectory is bit-identical whatever the other boxes, the cluster size C
+ * and the block size are (unless the Newton-3 option is set).  They agree
+ * with dpd.h's engine to FP32 rounding, not bit for bit (different
+ * summation order).
  *
  * Limits: a box must fit in one CTA's shared memory (about 4,000 particles
  * with lambda = 1/2, about 3,200 otherwise; dpd_ensemble_fits tells), have at
