@@ -40,7 +40,11 @@ typedef struct dpd_sim dpd_sim; /* opaque handle */
 typedef enum {
     DPD_OK = 0,
     DPD_ERR_ARG = 1,          /* invalid argument; nothing changed */
-    DPD_ERR_OOM = 2,          /* device or host allocation failed */
+    DPD_ERR_OOM = 2,          /* device or host allocation failed (a call that fails
+                                 this way while staging its input changes no state;
+                                 for tests, the environment variable
+                                 DPD_TEST_FAIL_ALLOC=1 makes every device allocation
+                                 of a handle fail this way) */
     DPD_ERR_CUDA = 3,         /* a CUDA call failed (latched) */
     DPD_ERR_NBR_OVERFLOW = 4, /* a group of 32 particles had more pairs than its list holds */
     DPD_ERR_NONFINITE = 5,    /* a force or position became NaN / Inf */
@@ -274,8 +278,9 @@ typedef struct {
     double body_force[3];
 } dpd_static_params;
 
-/* Total pair force (Eqs. 2-9, plus the body force; no bonds) on n particles
- * at one step, with no device allocation.  All arrays are DEVICE pointers
+/* The same total force as dpd_forces gives for this state (DPD pair forces
+ * and the body force; no bonds) on n particles at one step, with no device
+ * allocation.  All arrays are DEVICE pointers
  * owned by the caller, in the caller's order:
  *   pos:       n x 4 floats (x, y, z in [0, L), species as int bits)
  *   vel:       n x 4 floats (vx, vy, vz, unused)
@@ -293,6 +298,11 @@ typedef struct {
  * Every call reuses the same array (the cell counts are cleared at the start
  * of each call), so calls whose kernels overlap on the GPU -- on different
  * streams, or from different host threads without ordering -- race on it.
+ * The force sums run in a fixed order, so repeated calls on the same input
+ * give the same bits.  A species outside 0..n_species-1 is not read from
+ * the parameter table: the force of that particle, and of every particle
+ * within rc of it, is written as NaN (the call itself still returns
+ * DPD_OK, since it does not wait for the kernels).
  * Errors: DPD_ERR_ARG for invalid or oversized input, DPD_ERR_CUDA for a
  * failed launch; dpd_forces_static_last_error() describes the failure. */
 dpd_status dpd_forces_static(const dpd_static_params *params, int64_t n, const float *pos, const float *vel,

@@ -92,6 +92,8 @@ def lib():
             L.oc_gauss.restype = f64
             L.oc_xi.argtypes = [u64, u64, u32, u32]
             L.oc_xi.restype = f64
+            L.oc_pair_hash_batch.argtypes = [u64, u64, i64, P(u32), P(u32), P(u32)]
+            L.oc_pair_hash_batch.restype = None
             L.oc_xi_batch.argtypes = [u64, u64, i64, P(u32), P(u32), P(f64)]
             L.oc_xi_batch.restype = None
             L.oc_fp32_d2.argtypes = [P(ctypes.c_float), P(ctypes.c_float), P(ctypes.c_float)]
@@ -150,6 +152,16 @@ def gauss(a: int, b: int) -> float:
 
 def xi(seed: int, step: int, tag_i: int, tag_j: int) -> float:
     return float(lib().oc_xi(seed, step, tag_i, tag_j))
+
+
+def pair_hash_batch(seed: int, step: int, ti, tj) -> np.ndarray:
+    """(m, 2) uint32 pair-hash words of Sec. 3.5 for the tag pairs (ti[k], tj[k])."""
+    ti = np.ascontiguousarray(ti, np.uint32)
+    tj = np.ascontiguousarray(tj, np.uint32)
+    out = np.zeros((ti.shape[0], 2), np.uint32)
+    lib().oc_pair_hash_batch(seed, step, ti.shape[0], _ptr(ti, ctypes.c_uint32), _ptr(tj, ctypes.c_uint32),
+                             _ptr(out, ctypes.c_uint32))
+    return out
 
 
 def xi_batch(seed: int, step: int, ti, tj) -> np.ndarray:

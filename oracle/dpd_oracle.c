@@ -164,6 +164,14 @@ void oc_xi_batch(uint64_t seed, uint64_t step, int64_t m, const uint32_t *ti, co
     for (int64_t k = 0; k < m; ++k) out[k] = oc_xi(seed, step, ti[k], tj[k]);
 }
 
+/* The pair-hash words for many pairs at one step (Sec. 3.5):
+ * out[2k], out[2k + 1] = oc_pair_hash(seed, step, ti[k], tj[k]). */
+void oc_pair_hash_batch(uint64_t seed, uint64_t step, int64_t m, const uint32_t *ti, const uint32_t *tj,
+                        uint32_t *out)
+{
+    for (int64_t k = 0; k < m; ++k) oc_pair_hash(seed, step, ti[k], tj[k], out + 2 * k);
+}
+
 /* ------------------------------------------------------------------------ */
 /* FP32 pair predicate (Sec. 3.4: the neighbour builder works in single      */
 /* precision).  Every operation is rounded on its own, in this order:        */

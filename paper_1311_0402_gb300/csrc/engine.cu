@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -185,9 +186,21 @@ void keep_pool_memory()
     if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold) != cudaSuccess) cudaGetLastError();
 }
 
+// Host-side allocation-failure injection for the failure tests: while the
+// environment variable DPD_TEST_FAIL_ALLOC is "1", every device allocation a
+// handle asks for reports failure without reaching the allocator, so the
+// out-of-memory paths run with no GPU fault and no real memory pressure.
+bool alloc_refused()
+{
+    const char *e = std::getenv("DPD_TEST_FAIL_ALLOC");
+    return e && e[0] == '1' && e[1] == '\0';
+}
+
 dpd_status dev_alloc(dpd_sim *h, void **p, size_t bytes, std::vector<void *> &list)
 {
     if (bytes == 0) bytes = 16;
+    if (alloc_refused())
+        return fail(h, DPD_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes refused (DPD_TEST_FAIL_ALLOC)");
     cudaError_t e = cudaMallocAsync(p, bytes, h->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -214,6 +227,7 @@ struct Staging {
     void *get(size_t bytes)
     {
         void *p = nullptr;
+        if (err == cudaSuccess && alloc_refused()) err = cudaErrorMemoryAllocation;
         if (err == cudaSuccess) err = cudaMallocAsync(&p, bytes ? bytes : 16, h->stream);
         if (err != cudaSuccess) {
             cudaGetLastError();

@@ -32,7 +32,8 @@ constexpr int kNAThreads = 256;
 // scratch layout (byte offsets, 256-aligned)
 constexpr size_t kOffKey = 0;                                          // u32 [max particles]
 constexpr size_t kOffIdx = kOffKey + 4 * (size_t)kNAMaxParticles;     // u32 [max particles]
-constexpr size_t kOffSig = kOffIdx + 4 * (size_t)kNAMaxParticles;     // u32 [max particles]
+constexpr size_t kOffFill = kOffIdx + 4 * (size_t)kNAMaxParticles;    // u32 [max particles]
+constexpr size_t kOffSig = kOffFill + 4 * (size_t)kNAMaxParticles;    // u32 [max particles]
 constexpr size_t kOffCount = kOffSig + 4 * (size_t)kNAMaxParticles;   // u32 [max cells]
 constexpr size_t kOffStart = kOffCount + 4 * (size_t)kNAMaxCells;     // u32 [max cells + 1]
 constexpr size_t kScratchBytes = kOffStart + 4 * ((size_t)kNAMaxCells + 64);
@@ -55,7 +56,10 @@ struct NAParams {
 };
 
 struct NAScratch {
-    uint32_t *key, *idx, *sig, *count, *start;
+    uint32_t *key;    // cell of each particle
+    uint32_t *fill;   // cell members in the order the atomics placed them
+    uint32_t *idx;    // cell members in index order
+    uint32_t *sig, *count, *start;
 };
 
 __device__ __forceinline__ int na_cell_axis(float x, float cpl, int nc)
@@ -128,25 +132,23 @@ __global__ void k_na_fill(NAParams P, NAScratch S)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
         uint32_t c = S.key[i];
-        S.idx[S.start[c] + atomicAdd(&S.count[c], 1u)] = (uint32_t)i;
+        S.fill[S.start[c] + atomicAdd(&S.count[c], 1u)] = (uint32_t)i;
     }
 }
 
-// Insertion sort of each cell's entries by particle index, so the force sums
-// run in a fixed order whatever order the atomics filled the cells in.
-__global__ void k_na_sortcell(NAParams P, NAScratch S)
+// Each particle's place in its cell is the number of members with a smaller
+// index, so idx[] holds every cell in index order whatever order the atomics
+// filled it in, and the force sums run in a fixed order.  One thread per
+// particle reads its own cell once: no thread does more than the cell's
+// occupancy in work.
+__global__ void k_na_rank(NAParams P, NAScratch S)
 {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += gridDim.x * blockDim.x) {
-        uint32_t b = S.start[c], e = S.start[c + 1];
-        for (uint32_t a = b + 1; a < e; ++a) {
-            uint32_t v = S.idx[a];
-            uint32_t q = a;
-            while (q > b && S.idx[q - 1] > v) {
-                S.idx[q] = S.idx[q - 1];
-                --q;
-            }
-            S.idx[q] = v;
-        }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const uint32_t c = S.key[i];
+        const uint32_t b = S.start[c], e = S.start[c + 1];
+        uint32_t r = 0;
+        for (uint32_t q = b; q < e; ++q) r += S.fill[q] < (uint32_t)i ? 1u : 0u;
+        S.idx[b + r] = (uint32_t)i;
     }
 }
 
@@ -161,6 +163,9 @@ __global__ void k_na_force(NAParams P, NAScratch S, const float4 *pos, const flo
     const float4 vi = vel[i];
     const uint32_t si = S.sig[i];
     const int ti = __float_as_int(pi.w);
+    // a species outside 0..n_species-1 (in this particle or a partner within
+    // r_c) makes the force NaN; the parameter table is never read with it
+    bool bad = (unsigned)ti >= (unsigned)P.n_species;
     const int cx = na_cell_axis(pi.x, P.cells_per_len[0], P.nc[0]);
     const int cy = na_cell_axis(pi.y, P.cells_per_len[1], P.nc[1]);
     const int cz = na_cell_axis(pi.z, P.cells_per_len[2], P.nc[2]);
@@ -198,7 +203,12 @@ __global__ void k_na_force(NAParams P, NAScratch S, const float4 *pos, const flo
                     uint32_t A, B;
                     pair_hash(si, S.sig[j], P.key, A, B);
                     const float xi = gauss_from_hash(A, B);
-                    const float a = P.a[ti * P.n_species + __float_as_int(pj.w)];
+                    const int tj = __float_as_int(pj.w);
+                    if (bad || (unsigned)tj >= (unsigned)P.n_species) {
+                        bad = true;
+                        continue;
+                    }
+                    const float a = P.a[ti * P.n_species + tj];
                     const float F = fmaf(a, w, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
                     const float sc = -F * inv_r;
                     fx = fmaf(sc, dx, fx);
@@ -212,6 +222,7 @@ __global__ void k_na_force(NAParams P, NAScratch S, const float4 *pos, const flo
         const float sg = pi.y < P.halfL[1] ? 1.0f : -1.0f;
         fx = fmaf(sg, P.body[0], fx); fy = fmaf(sg, P.body[1], fy); fz = fmaf(sg, P.body[2], fz);
     }
+    if (bad) fx = fy = fz = __int_as_float(0x7FC00000);  // quiet NaN
     fout[i] = make_float4(fx, fy, fz, 0.0f);
 }
 
@@ -307,6 +318,7 @@ dpd_status dpd_forces_static(const dpd_static_params *prm, int64_t n, const floa
     NAScratch S;
     S.key = (uint32_t *)(b + kOffKey);
     S.idx = (uint32_t *)(b + kOffIdx);
+    S.fill = (uint32_t *)(b + kOffFill);
     S.sig = (uint32_t *)(b + kOffSig);
     S.count = (uint32_t *)(b + kOffCount);
     S.start = (uint32_t *)(b + kOffStart);
@@ -321,7 +333,7 @@ dpd_status dpd_forces_static(const dpd_static_params *prm, int64_t n, const floa
     k_na_bin<<<gn, kNAThreads, 0, s>>>(P, S, p4, tag);
     k_na_scan<<<1, 1024, 0, s>>>(P, S);
     k_na_fill<<<gn, kNAThreads, 0, s>>>(P, S);
-    k_na_sortcell<<<gc, kNAThreads, 0, s>>>(P, S);
+    k_na_rank<<<gn, kNAThreads, 0, s>>>(P, S);
     switch (P.s_mode) {
     case 1: k_na_force<1><<<gn, kNAThreads, 0, s>>>(P, S, p4, v4, f4); break;
     case 2: k_na_force<2><<<gn, kNAThreads, 0, s>>>(P, S, p4, v4, f4); break;

@@ -170,3 +170,128 @@ def test_bounded_device_wait_reports_timeout_and_recovers():
     x32, v32, step = g.state()
     fo, _ = o.forces(x32, v32, step=step)
     assert force_error(g.forces(), fo)[0] < 1e-4
+
+
+def _edge_units(L, rl):
+    """Pairs of particles whose FP32 predicate distance d^2 is exactly
+    fp32(r_list)^2, one ulp below it and one ulp above it, each pair straddling
+    a periodic face (x, y and z in turn).  Built by a search over FP32
+    positions with the predicate's rounding (numpy float32 arithmetic, every
+    operation rounded on its own); the oracle then decides membership."""
+    f32 = np.float32
+    Lf, h = f32(L), f32(0.5) * f32(L)
+    rl2 = f32(f32(rl) * f32(rl))
+    targets = {"eq": rl2, "prev": np.nextafter(rl2, f32(0)), "next": np.nextafter(rl2, f32(10))}
+
+    def d2(a, b):
+        d = []
+        for k in range(3):
+            t = f32(b[k] - a[k])
+            t = f32(t - Lf) if t > h else (f32(t + Lf) if t < -h else t)
+            d.append(t)
+        return f32(f32(f32(d[0] * d[0]) + f32(d[1] * d[1])) + f32(d[2] * d[2]))
+
+    units = []
+    slots = {"eq": (4.5, 4.5), "prev": (4.5, 7.5), "next": (7.5, 4.5)}
+    for axis in range(3):
+        other, third = (axis + 1) % 3, (axis + 2) % 3
+        for name, tgt in targets.items():
+            hit = None
+            for base_t in np.linspace(rl - 0.02, rl - 0.06, 41):
+                for high_side in (True, False):
+                    xi = np.zeros(3, f32)
+                    xi[other], xi[third] = f32(slots[name][0]), f32(slots[name][1])
+                    xi[axis] = f32(L - 0.35) if high_side else f32(0.3)
+                    xj = xi.copy()
+                    xj[axis] = f32((float(xi[axis]) + (base_t if high_side else -base_t)) % L)
+                    need = float(tgt) - float(d2(xi, xj))
+                    y0 = f32(float(xi[other]) + np.sqrt(need))
+                    cands, a, b = [y0], y0, y0
+                    for _ in range(30):
+                        a, b = np.nextafter(a, f32(-1)), np.nextafter(b, f32(100))
+                        cands += [a, b]
+                    for y in cands:
+                        x2 = xj.copy()
+                        x2[other] = y
+                        if d2(xi, x2) == tgt:
+                            hit = (xi, x2)
+                            break
+                    if hit:
+                        break
+                if hit:
+                    break
+            assert hit is not None, (axis, name)
+            units.append((name, hit[0], hit[1]))
+    return units, targets
+
+
+@pytest.mark.parametrize("deterministic", [0, 1])
+def test_neighbor_predicate_edges_across_periodic_faces(deterministic):
+    """Pairs placed at d^2 = r_list^2 and one ulp either side of it, across the
+    periodic faces: the GPU builder keeps exactly the pairs the oracle's FP32
+    predicate keeps (strict d^2 < r_list^2)."""
+    L = 12.0
+    cfg = dict(CFG, box=(L, L, L))
+    units, targets = _edge_units(L, cfg["rc"] + 0.3)
+    x = np.array([p for _, a, b in units for p in (a, b)], np.float64)
+    g, _ = make_pair(cfg, box=cfg["box"], deterministic=deterministic)
+    g.set_state(x, np.zeros_like(x))
+    x32, _, _ = g.state()
+    assert np.array_equal(x32, x)  # the FP32 positions arrive unchanged
+    ref = oracle.pairs_fp32(x32, cfg["box"], cfg["rc"] + 0.3)
+    # the construction hits the edge: each unit's own distance is the target
+    for k, (name, a, b) in enumerate(units):
+        assert np.float32(oracle.fp32_d2(a, b, cfg["box"])) == targets[name]
+    want = {(2 * k, 2 * k + 1) for k, (name, _, _) in enumerate(units) if name == "prev"}
+    assert pair_set(ref) == pair_set(np.array(sorted(want), np.uint32))
+    assert pair_set(g.neighbors()) == pair_set(ref)
+    g.close()
+
+
+def test_allocation_failure_leaves_handle_unchanged(monkeypatch):
+    """Host-made allocation failure (DPD_TEST_FAIL_ALLOC=1 refuses every
+    device allocation without reaching the allocator): creating a handle and
+    loading a state report DPD_ERR_OOM, and a handle whose load was refused
+    keeps its previous state and goes on stepping."""
+    st = workloads.make("fluid_small")
+    c = st["cfg"]
+    g, o = make_pair(c)
+    g.set_state(st["x"], st["v"], step=3)
+    x0, v0, s0 = g.state()
+    monkeypatch.setenv("DPD_TEST_FAIL_ALLOC", "1")
+    with pytest.raises(dpd.DPDError) as e:
+        dpd.Sim(c["box"], c["a"], c["gamma"], c["kT"], c["rc"], c["s"], c["dt"])
+    assert e.value.status == 2  # DPD_ERR_OOM
+    with pytest.raises(dpd.DPDError) as e:
+        g.set_state(st["x"][::-1].copy(), st["v"][::-1].copy(), step=77)
+    assert e.value.status == 2
+    monkeypatch.delenv("DPD_TEST_FAIL_ALLOC")
+    x1, v1, s1 = g.state()
+    assert s1 == s0 and np.array_equal(x1, x0) and np.array_equal(v1, v0)
+    g.step(5)
+    x2, v2, s2 = g.state()
+    fo, _ = o.forces(x2, v2, step=s2)
+    assert s2 == s0 + 5 and force_error(g.forces(), fo)[0] < 1e-4
+    g.close()
+
+
+@pytest.mark.parametrize("deterministic", [0, 1])
+def test_force_overflow_during_a_step_latches_nonfinite(deterministic):
+    """Finite inputs whose force overflows FP32 inside a step: two particles
+    1.3 apart (no force at load) close to 0.4 in the first step, where the
+    conservative term a w / r with a = 3e38 exceeds the FP32 range.  The
+    device latches its non-finite flag, dpd_step returns DPD_ERR_NONFINITE,
+    and the handle accepts a new state afterwards."""
+    c = dict(CFG, a=[[3.0e38]])
+    g, _ = make_pair(c, deterministic=deterministic)
+    x = np.array([[5.0, 5.0, 5.0], [6.3, 5.0, 5.0]])
+    v = np.array([[45.0, 0.0, 0.0], [-45.0, 0.0, 0.0]])
+    g.set_state(x, v)
+    assert np.all(np.isfinite(g.forces()))
+    with pytest.raises(dpd.DPDError) as e:
+        g.step(1)
+    assert e.value.status == 5  # DPD_ERR_NONFINITE
+    g.set_state(np.array([[5.0, 5.0, 5.0], [7.0, 5.0, 5.0]]), np.zeros((2, 3)))
+    g.step(2)
+    assert np.all(np.isfinite(g.state()[0]))
+    g.close()

@@ -79,6 +79,19 @@ def test_pair_hash_symmetric_and_keyed():
     assert oracle.pair_hash(42, 5, 3, 8) == oracle.tea(4, oracle.key(42), min(si, sj), max(si, sj))
 
 
+def test_pair_hash_batch_is_the_per_pair_hash():
+    # the batched call (used for the all-pairs GPU comparison) marshals the
+    # same per-pair routine: composition from the signatures, symmetric
+    rng = np.random.default_rng(3)
+    ti = rng.integers(0, 2**32, 64, dtype=np.uint64).astype(np.uint32)
+    tj = rng.integers(0, 2**32, 64, dtype=np.uint64).astype(np.uint32)
+    hb = oracle.pair_hash_batch(42, 11, ti, tj)
+    for k in range(64):
+        si, sj = oracle.signature(42, int(ti[k]), 11), oracle.signature(42, int(tj[k]), 11)
+        assert tuple(int(w) for w in hb[k]) == oracle.tea(4, oracle.key(42), min(si, sj), max(si, sj))
+    assert np.array_equal(hb, oracle.pair_hash_batch(42, 11, tj, ti))
+
+
 def test_box_muller_special_values():
     # u1 = 1 (a = 2^32 - 1): radius sqrt(-2 ln 1) = 0
     assert oracle.gauss(0xFFFFFFFF, 12345) == 0.0
