@@ -67,7 +67,8 @@ def parse():
                     help="boxes of the ensemble-kernel leg (0 skips it)")
     ap.add_argument("--no-tune", action="store_true", help="skip the skin tuner's measurement of the 3M system")
     ap.add_argument("--ablations", action="store_true",
-                    help="also time the atomic-insertion list builder against the ballot one (Table 2)")
+                    help="also time the atomic-insertion list builder against the ballot one (Table 2), "
+                         "reorder on/off and the paper's row list layout against the packed lists")
     ap.add_argument("--no-conditional", action="store_true",
                     help="launch the rebuild chain in every step's graph (for profilers that do not enter "
                          "conditional graph nodes)")
@@ -485,6 +486,30 @@ def run_list_ablation():
     return out
 
 
+def run_layout_ablation():
+    """The paper's list layout (Sec. 3.3: rows per particle written with core
+    pairs in front and skin pairs at the back, joined, 32 x 32 tiles
+    transposed, one thread per particle in the pair force, full lists) against
+    the packed group lists, on the 3M fluid: the packed lists with each pair
+    once (the default) and with full lists in fixed order (the same work as
+    the paper's layout)."""
+    import paper_1311_0402_gb300 as dpd
+    import workloads
+    st = workloads.make("fluid_large")
+    c = st["cfg"]
+    out = {"workload": "fluid_large (3M), skin %g, 200 steps after 20" % workloads.BENCH_SKIN}
+    for name, layout, det in (("packed_newton3", 0, 0), ("packed_full_lists", 0, 1), ("rows_paper_layout", 1, 1)):
+        sim = dpd.Sim(c["box"], c["a"], c["gamma"], c["kT"], c["rc"], c["s"], c["dt"], skin=workloads.BENCH_SKIN,
+                      deterministic=det, list_layout=layout)
+        sim.set_state(st["x"], st["v"])
+        sim.step(20)
+        t = sim.step_profiled(200)
+        sim.close()
+        out[name] = {"ms_per_step": t["total_ms"] / 200, "pair_ms": t["pair_ms"] / 200,
+                     "rebuild_ms_per_rebuild": t["rebuild_ms"] / max(t["rebuilds"], 1), "rebuilds": t["rebuilds"]}
+    return out
+
+
 def run_reorder_ablation():
     """The paper's reorder on/off comparison (Sec. 3.2) on the 3M fluid: the
     whole step with the particles reordered into cell order at every rebuild
@@ -654,6 +679,7 @@ def main():
     if rank == 0 and ws == 1 and args.ablations:
         line["list_builder_ablation"] = run_list_ablation()
         line["reorder_ablation"] = run_reorder_ablation()
+        line["list_layout_ablation"] = run_layout_ablation()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -88,6 +88,17 @@ typedef struct {
                                  into cell order (Sec. 3.2); 1: they stay in load order and
                                  the list is built through the sort permutation -- the
                                  paper's reorder on/off comparison (Sec. 3.2); slower */
+    int32_t list_layout;      /* 0 (default): packed lists per group of 32 particles (see
+                                 nbr_capacity), consumed 32 entries at a time; 1: the
+                                 paper's layout (Sec. 3.3): one row of nbr_capacity entries
+                                 per particle, written row-major by the builder with the
+                                 pairs inside r_c at build time from the front of the row
+                                 and the skin pairs from its back (double insertion), the
+                                 two parts joined by a second kernel, each 32 x 32 tile of
+                                 the table transposed in place by a third, and the pair
+                                 force evaluated by one thread per particle walking its row
+                                 (every pair by both particles, fixed order).  Layout 1
+                                 needs at least 3 cells along every axis. */
     double wait_timeout_s;    /* host wait limit per call (default 600 s) */
     void *stream;             /* cudaStream_t to run on; NULL = a stream of the handle */
 } dpd_options;

@@ -91,9 +91,18 @@ dpd_status dpd_ensemble_remove(dpd_ensemble *e, int32_t id);
 
 /* Advance box ids[k] by steps[k] steps (steps[k] >= 0) for k < m, all in
  * one launch per size class; ids == NULL with m == 0 advances every box by
- * steps[0].  Returns after queueing (asynchronous); dpd_ensemble_sync waits
- * and reports device-side errors (a non-finite force: DPD_ERR_NONFINITE). */
+ * steps[0].  The class launches (forked onto one stream per class and
+ * joined back) are captured as a CUDA graph and the graph is replayed by
+ * later calls with the same launch structure -- the same boxes per class,
+ * whatever their step counts, which the launches read from device
+ * descriptors uploaded before each replay; a new structure is captured
+ * anew.  So the handle's stream must not itself be under capture.  Returns
+ * after queueing (asynchronous); dpd_ensemble_sync waits and reports
+ * device-side errors (a non-finite force: DPD_ERR_NONFINITE). */
 dpd_status dpd_ensemble_step(dpd_ensemble *e, const int32_t *ids, const int32_t *steps, int32_t m);
+
+/* How many step calls captured a new graph and how many replayed one. */
+dpd_status dpd_ensemble_graph_stats(dpd_ensemble *e, int64_t *captures, int64_t *replays);
 
 /* Wait for everything queued on the ensemble (deadline wait_timeout_s). */
 dpd_status dpd_ensemble_sync(dpd_ensemble *e);

@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdpd.so")
+# DPD_LIB_VARIANT=checked loads the checked build (device index checks, see
+# buildlib); the default is the production library
+LIB_PATH = os.path.join(HERE, "libdpd_checked.so" if os.environ.get("DPD_LIB_VARIANT") == "checked" else "libdpd.so")
 
 DPD_OK = 0
 STATUS = {0: "DPD_OK", 1: "DPD_ERR_ARG", 2: "DPD_ERR_OOM", 3: "DPD_ERR_CUDA", 4: "DPD_ERR_NBR_OVERFLOW",
@@ -34,6 +36,7 @@ EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds"
            "dpd_ensemble_default_options", "dpd_ensemble_create", "dpd_ensemble_fits", "dpd_ensemble_add",
            "dpd_ensemble_remove", "dpd_ensemble_step", "dpd_ensemble_sync", "dpd_ensemble_get_state",
            "dpd_ensemble_get_forces", "dpd_ensemble_observables", "dpd_ensemble_info", "dpd_ensemble_tune",
+           "dpd_ensemble_graph_stats",
            "dpd_ensemble_config", "dpd_ensemble_destroy", "dpd_ensemble_last_error")
 
 
@@ -57,6 +60,7 @@ class dpd_options(ctypes.Structure):
         ("conditional_rebuild", ctypes.c_int32),
         ("list_builder", ctypes.c_int32),
         ("no_reorder", ctypes.c_int32),
+        ("list_layout", ctypes.c_int32),
         ("wait_timeout_s", ctypes.c_double),
         ("stream", ctypes.c_void_p),
     ]
@@ -181,7 +185,7 @@ _lib = None
 
 def build(force: bool = False, verbose: bool = False) -> str:
     from . import buildlib as _b
-    return _b.build(force=force, verbose=verbose)
+    return _b.build(force=force, verbose=verbose, checked=os.path.basename(LIB_PATH) == "libdpd_checked.so")
 
 
 def lib():
@@ -189,7 +193,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libdpd.so is not built (run paper_1311_0402_gb300.build())")
+            raise RuntimeError("%s is not built (run paper_1311_0402_gb300.build())" % os.path.basename(LIB_PATH))
         L = ctypes.CDLL(LIB_PATH)
         P = ctypes.POINTER
         i32, i64, u32, u64, f64, vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
@@ -250,6 +254,7 @@ def lib():
         L.dpd_ensemble_get_forces.argtypes = [vp, i32, P(f64)]
         L.dpd_ensemble_observables.argtypes = [vp, i32, P(dpd_obs)]
         L.dpd_ensemble_info.argtypes = [vp, P(i32), P(i64)]
+        L.dpd_ensemble_graph_stats.argtypes = [vp, P(i64), P(i64)]
         L.dpd_ensemble_tune.argtypes = [vp, i32, P(f64)]
         L.dpd_ensemble_config.argtypes = [vp, P(i32), P(i32)]
         L.dpd_ensemble_destroy.argtypes = [vp]
@@ -479,7 +484,7 @@ class Sim:
 
     def __init__(self, box, a_ij, gamma, kT, rc, s, dt, lam=0.5, skin=0.3, seed=42, body_mode=0,
                  body=(0.0, 0.0, 0.0), rebuild_every=0, nbr_capacity=0, graph_steps=8, stream=None,
-                 deterministic=0, conditional_rebuild=1, list_builder=0, no_reorder=0):
+                 deterministic=0, conditional_rebuild=1, list_builder=0, no_reorder=0, list_layout=0):
         o = dpd_default_options()
         o.skin = skin
         o.lam = lam
@@ -493,6 +498,7 @@ class Sim:
         o.conditional_rebuild = 1 if conditional_rebuild else 0
         o.list_builder = int(list_builder)
         o.no_reorder = 1 if no_reorder else 0
+        o.list_layout = int(list_layout)
         o.stream = stream
         self.box = np.asarray(box, np.float64)
         self.h = dpd_create(box, a_ij, gamma, kT, rc, s, dt, o)
@@ -750,6 +756,12 @@ class Ensemble:
         nb, npart = ctypes.c_int32(), ctypes.c_int64()
         _ens_check(lib().dpd_ensemble_info(self.e, ctypes.byref(nb), ctypes.byref(npart)), self.e)
         return nb.value, npart.value
+
+    def graph_stats(self):
+        """(step calls that captured a new launch graph, calls that replayed one)."""
+        c, r = ctypes.c_int64(), ctypes.c_int64()
+        _ens_check(lib().dpd_ensemble_graph_stats(self.e, ctypes.byref(c), ctypes.byref(r)), self.e)
+        return c.value, r.value
 
     def tune(self, steps=50):
         """Autotune threads per CTA and CTAs per box for each size class

@@ -43,6 +43,16 @@ constexpr int kBrick = 4;
 constexpr int kHalo = kBrick + 2;
 constexpr int kHaloCells = kHalo * kHalo * kHalo;  // 216
 
+// The checked build (compiled with DPD_CHECKED): kernels test the indices
+// they read from device memory (list entries, permutations, bond partners)
+// against the particle count before using them, skip a bad one and set
+// kErrBadIndex, which the host reports.  The production build trusts them.
+#ifdef DPD_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
 // device error bits
 constexpr uint32_t kErrNbrOverflow = 1u;
 constexpr uint32_t kErrNonFinite = 2u;
@@ -94,6 +104,8 @@ struct SimParams {
     int use_bricks;           // every axis has >= 3 cells: the brick-staged builder
     int list_builder;         // 0: ballot insertion; 1: atomic insertion (ablation)
     int no_reorder;           // 1: particles stay in load order (ablation; tile builder, no bricks)
+    int list_layout;          // 0: packed group lists; 1: rows per particle (double insertion, join,
+                              // 32x32 tile transpose; full lists, one thread per particle in the force)
     int brick_cap;            // halo particles the brick builder stages in shared memory
     int nb[3];                // bricks per axis
     int nbricks;
@@ -121,6 +133,7 @@ struct Ptrs {
     // neighbours
     uint32_t *nbr;                 // packed group lists, [ngroups][gcap]
     uint2 *gdesc;                  // [ngroups] (first particle, owners | entries << 6)
+    uint32_t *rowcnt;              // list_layout 1: [n] row length (core | skin << 16 until the join)
     // bricks
     const uint32_t *brick_rank_lo; // [nbricks] first Morton rank of the brick's cells
     const uint32_t *brick_rank_hi; // [nbricks] last Morton rank (inclusive)

@@ -11,6 +11,8 @@
 #include "dpd.h"
 #include "dpd_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -150,6 +152,13 @@ struct dpd_sim {
 
 namespace {
 
+// An NVTX range over one API call, for profilers that record NVTX (the
+// kernels of the call appear inside it on the timeline).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 dpd_status fail(dpd_sim *h, dpd_status st, const std::string &msg)
 {
     if (h) {
@@ -284,6 +293,8 @@ dpd_status check_err(dpd_sim *h, DevCtl &c)
                         std::to_string(h->P.gcap));
     if (c.err & kErrNonFinite) return fail(h, DPD_ERR_NONFINITE, "non-finite force");
     if (c.err & kErrTimeout) return fail(h, DPD_ERR_TIMEOUT, "a device-side wait for staged data ran out");
+    if (c.err & kErrBadIndex)
+        return fail(h, DPD_ERR_STATE, "a kernel met a list entry outside the particle range (the access was skipped)");
     return DPD_OK;
 }
 
@@ -509,6 +520,7 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     A((void **)&D.idx_of_pid, u4);
     h->P.ngroups = group_count(h, n);
     A((void **)&D.gdesc, sizeof(uint2) * (size_t)h->P.ngroups);
+    A((void **)&D.rowcnt, u4);
     A((void **)&D.nbr, (size_t)h->P.ngroups * kGroup * (size_t)cap * sizeof(uint32_t));
     h->red_doubles = std::max<size_t>((size_t)observe_blocks_for((int)n) * 8 + 8, 4096);
     A((void **)&D.vir_part, sizeof(double) * (size_t)((h->P.ngroups + kForceWarps - 1) / kForceWarps));
@@ -517,6 +529,10 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     if (st) return st;
     CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(D.gdesc, 0, sizeof(uint2) * (size_t)h->P.ngroups, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(D.rowcnt, 0, u4, h->stream));
+    // partials of a pair kernel launched with fewer blocks than the largest count stay zero
+    CUDA_TRY(h, cudaMemsetAsync(D.vir_part, 0, sizeof(double) * (size_t)((h->P.ngroups + kForceWarps - 1) / kForceWarps),
+                                h->stream));
     CUDA_TRY(h, cudaMemsetAsync(D.facc, 0, f4, h->stream));
     h->P.cap = cap;
     h->P.gcap = kGroup * cap;
@@ -536,8 +552,10 @@ dpd_status rebuild_and_force(dpd_sim *h, bool grow_on_overflow)
         DevCtl c;
         dpd_status st = check_err(h, c);
         if (st != DPD_ERR_NBR_OVERFLOW || !grow_on_overflow) return st;
-        // grow the list: keep the particle arrays, reallocate the table
-        const int cap = capacity_for_total(c.max_nnb);
+        // grow the list: keep the particle arrays, reallocate the table (the
+        // row layout reports its longest row, the packed one its largest group)
+        const int cap = h->P.list_layout == 1 ? ((int)((uint64_t)c.max_nnb * 5 / 4 + 8) + 31) / 32 * 32
+                                              : capacity_for_total(c.max_nnb);
         if ((int64_t)cap * kGroup >= (int64_t(1) << 26))
             return fail(h, DPD_ERR_NBR_OVERFLOW, "neighbour list overflow: group list beyond 2^26 entries");
         dev_free(h, h->D.nbr, h->allocs);
@@ -619,6 +637,7 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     if (o.body_force_mode < 0 || o.body_force_mode > 2) return fail(nullptr, DPD_ERR_ARG, "body_force_mode in 0..2");
     if (o.list_builder < 0 || o.list_builder > 1) return fail(nullptr, DPD_ERR_ARG, "list_builder in 0..1");
     if (o.no_reorder < 0 || o.no_reorder > 1) return fail(nullptr, DPD_ERR_ARG, "no_reorder in 0..1");
+    if (o.list_layout < 0 || o.list_layout > 1) return fail(nullptr, DPD_ERR_ARG, "list_layout in 0..1");
     if (o.rebuild_every < 0 || o.graph_steps < 0 || o.nbr_capacity < 0 || !(o.wait_timeout_s > 0))
         return fail(nullptr, DPD_ERR_ARG, "rebuild_every, graph_steps, nbr_capacity >= 0; wait_timeout_s > 0");
     const double rl = rc + o.skin;
@@ -706,6 +725,16 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     h->n_scan_blocks = scan_blocks_for(P.ncell);
     P.no_reorder = o.no_reorder;
     P.use_bricks = (!o.no_reorder && nc[0] >= 3 && nc[1] >= 3 && nc[2] >= 3) ? 1 : 0;
+    // the paper's row layout: full lists built brick by brick, one thread per
+    // particle in the pair force
+    P.list_layout = o.list_layout;
+    if (o.list_layout == 1) {
+        if (!P.use_bricks) {
+            dpd_destroy(h);
+            return fail(nullptr, DPD_ERR_ARG, "list_layout 1 needs at least 3 cells along every axis and no_reorder 0");
+        }
+        P.newton3 = 0;
+    }
     P.list_builder = o.list_builder;
     for (int a = 0; a < 3; ++a) P.nb[a] = h->geo.nb[a];
     P.nbricks = h->geo.nb[0] * h->geo.nb[1] * h->geo.nb[2];
@@ -759,6 +788,7 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
 dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v, const int32_t *species,
                          const uint32_t *tag, uint64_t step)
 {
+    NvtxRange nvtx_("dpd_set_state");
     dpd_status st = guard(h, false);
     if (st) return st;
     if (n <= 0 || n > kMaxParticles || !x || !v) return fail(h, DPD_ERR_ARG, "need 0 < n <= 2^27 and x, v");
@@ -791,6 +821,7 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
     if (bad_h & 1u) return fail(h, DPD_ERR_ARG, "non-finite x or v");
     if (bad_h & 2u) return fail(h, DPD_ERR_ARG, "species out of range");
     int cap = h->opt.nbr_capacity > 0 ? h->opt.nbr_capacity : auto_capacity(h, n);
+    if (h->P.list_layout == 1) cap = (cap + 31) / 32 * 32;  // whole 32 x 32 tiles per row
     if (h->P.use_bricks) {
         // staging buffer of the brick builder: the expected halo population
         // with a wide margin; a brick beyond it reads global memory
@@ -862,6 +893,7 @@ dpd_status dpd_set_bonds(dpd_sim *h, int64_t nb, const uint32_t *pairs, double k
 
 dpd_status dpd_build_neighbors(dpd_sim *h)
 {
+    NvtxRange nvtx_("dpd_build_neighbors");
     dpd_status st = guard(h, true);
     if (st) return st;
     if (h->pending && (st = dpd_sync(h)) != DPD_OK) return st;  // report a queued run's error first
@@ -877,7 +909,7 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
     st = read_ctl(h, c);
     if (st) return st;
     const int64_t n = h->n;
-    const int G = h->P.ngroups;
+    int G = h->P.ngroups;
     std::vector<uint32_t> nbr((size_t)G * h->P.gcap), pid(n);
     std::vector<uint2> desc(G);
     CUDA_TRY(h, cudaMemcpyAsync(nbr.data(), h->D.nbr, sizeof(uint32_t) * nbr.size(), cudaMemcpyDeviceToHost, h->stream));
@@ -886,6 +918,26 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
     st = wait(h);
     if (st) return st;
     std::vector<uint64_t> pr;
+    if (h->P.list_layout == 1) {
+        // rows of the transposed table: entry k of particle i at row
+        // 32 (i / 32) + k % 32, entry 32 (k / 32) + i % 32
+        std::vector<uint32_t> rc(n);
+        CUDA_TRY(h, cudaMemcpyAsync(rc.data(), h->D.rowcnt, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
+        st = wait(h);
+        if (st) return st;
+        const size_t cap = (size_t)h->P.cap;
+        for (int64_t i = 0; i < n; ++i) {
+            if (rc[i] > cap) return fail(h, DPD_ERR_STATE, "row longer than its capacity");
+            for (uint32_t k = 0; k < rc[i]; ++k) {
+                const size_t at = ((size_t)(i / 32) * 32 + k % 32) * cap + (k / 32) * 32 + (size_t)(i % 32);
+                const uint32_t j = nbr[at];
+                if (j >= (uint32_t)n) return fail(h, DPD_ERR_STATE, "neighbour entry out of range");
+                const uint32_t a = std::min(pid[i], pid[j]), b2 = std::max(pid[i], pid[j]);
+                if (a != b2) pr.push_back(((uint64_t)a << 32) | b2);
+            }
+        }
+        G = 0;  // no group lists
+    }
     for (int g = 0; g < G; ++g) {
         const uint32_t first = desc[g].x, owners = desc[g].y & 63u, ne = desc[g].y >> 6;
         if (owners > (uint32_t)kGroup || ne > (uint32_t)h->P.gcap || (owners && first + owners > (uint64_t)n))
@@ -911,6 +963,7 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
 
 dpd_status dpd_forces(dpd_sim *h, double *f_out)
 {
+    NvtxRange nvtx_("dpd_forces");
     dpd_status st = guard(h, true);
     if (st) return st;
     if (h->pending && (st = dpd_sync(h)) != DPD_OK) return st;  // report a queued run's error first
@@ -961,6 +1014,7 @@ dpd_status dpd_set_force(dpd_sim *h, const double *f)
 
 dpd_status dpd_step_async(dpd_sim *h, int64_t nsteps)
 {
+    NvtxRange nvtx_("dpd_step_async");
     dpd_status st = guard(h, true);
     if (st) return st;
     if (nsteps < 0) return fail(h, DPD_ERR_ARG, "nsteps < 0");
@@ -995,6 +1049,7 @@ dpd_status dpd_step_async(dpd_sim *h, int64_t nsteps)
 
 dpd_status dpd_sync(dpd_sim *h)
 {
+    NvtxRange nvtx_("dpd_sync");
     dpd_status st = guard(h, true);
     if (st) return st;
     DevCtl c;
@@ -1046,6 +1101,7 @@ dpd_status dpd_step(dpd_sim *h, int64_t nsteps)
 
 dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
 {
+    NvtxRange nvtx_("dpd_step_profiled");
     dpd_status st = guard(h, true);
     if (st) return st;
     if (nsteps < 1 || nsteps > 100000) return fail(h, DPD_ERR_ARG, "nsteps must be in 1..100000");
@@ -1116,6 +1172,7 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *out)
 
 dpd_status dpd_observables(dpd_sim *h, dpd_obs *out)
 {
+    NvtxRange nvtx_("dpd_observables");
     dpd_status st = guard(h, true);
     if (st) return st;
     if (!out) return fail(h, DPD_ERR_ARG, "out is NULL");
@@ -1174,6 +1231,7 @@ dpd_status dpd_profile(dpd_sim *h, int32_t bin_axis, int32_t vel_axis, int32_t n
 
 dpd_status dpd_get_state(dpd_sim *h, double *x, double *v, uint64_t *step)
 {
+    NvtxRange nvtx_("dpd_get_state");
     dpd_status st = guard(h, true);
     if (st) return st;
     DevCtl c;

@@ -59,6 +59,13 @@ struct dpd_ensemble {
     size_t limit = 0;
     bool failed = false;
     std::string err;
+    // the fork / class launches / join sequence of the last step call,
+    // captured as a CUDA graph and replayed while the launch structure (the
+    // classes, box counts, descriptor offsets and launch shapes) repeats
+    cudaGraphExec_t graph = nullptr;
+    std::vector<uint64_t> graph_key;
+    int64_t graph_replays = 0;
+    int64_t graph_captures = 0;
 };
 
 namespace {
@@ -482,22 +489,62 @@ dpd_status dpd_ensemble_step(dpd_ensemble *e, const int32_t *ids, const int32_t 
     dpd_status st = ensure_desc(e, descs.size());
     if (st) return st;
     ENS_TRY(e, cudaMemcpyAsync(e->d_desc, descs.data(), descs.size() * sizeof(EnsBox), cudaMemcpyHostToDevice, e->stream));
-    ENS_TRY(e, cudaEventRecord(e->fork, e->stream));
-    bool used[kClasses] = {false, false, false, false};
+    // the launches read their descriptors (steps, step numbers) from d_desc,
+    // so one captured graph serves every call with the same structure
+    std::vector<uint64_t> key = {(uint64_t)(uintptr_t)e->d_desc, (uint64_t)descs.size(), (uint64_t)e->opt.newton3};
     for (const Launch &L : launches) {
-        cudaStream_t s = e->cls_stream[L.cls];
-        if (!used[L.cls]) {
-            ENS_TRY(e, cudaStreamWaitEvent(s, e->fork, 0));
-            used[L.cls] = true;
-        }
-        ENS_TRY(e, launch_ensemble(e->d_desc + L.off, L.nb, L.lhalf, L.s_mode, e->opt.newton3 != 0, L.shape.threads,
-                                   L.shape.cluster, L.shape.smem, s));
+        key.push_back((uint64_t)L.cls | ((uint64_t)L.lhalf << 8) | ((uint64_t)L.s_mode << 16) |
+                      ((uint64_t)L.shape.cluster << 24) | ((uint64_t)L.shape.threads << 32));
+        key.push_back((uint64_t)L.off | ((uint64_t)L.nb << 32));
+        key.push_back((uint64_t)L.shape.smem);
     }
-    for (int c = 0; c < kClasses; ++c)
-        if (used[c]) {
-            ENS_TRY(e, cudaEventRecord(e->join[c], e->cls_stream[c]));
-            ENS_TRY(e, cudaStreamWaitEvent(e->stream, e->join[c], 0));
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t err = cudaEventRecord(e->fork, e->stream);
+        bool used[kClasses] = {false, false, false, false};
+        for (const Launch &L : launches) {
+            if (err != cudaSuccess) break;
+            cudaStream_t s = e->cls_stream[L.cls];
+            if (!used[L.cls]) {
+                err = cudaStreamWaitEvent(s, e->fork, 0);
+                used[L.cls] = true;
+            }
+            if (err == cudaSuccess)
+                err = launch_ensemble(e->d_desc + L.off, L.nb, L.lhalf, L.s_mode, e->opt.newton3 != 0,
+                                      L.shape.threads, L.shape.cluster, L.shape.smem, s);
         }
+        for (int c = 0; c < kClasses && err == cudaSuccess; ++c)
+            if (used[c]) {
+                err = cudaEventRecord(e->join[c], e->cls_stream[c]);
+                if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->join[c], 0);
+            }
+        return err;
+    };
+    if (!(e->graph && key == e->graph_key)) {
+        if (e->graph) cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+        e->graph_key.clear();
+        cudaGraph_t g = nullptr;
+        ENS_TRY(e, cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ce = enqueue();
+        const cudaError_t ee = cudaStreamEndCapture(e->stream, &g);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return efail(e, DPD_ERR_CUDA, std::string("graph capture of the ensemble launches: ") +
+                                              cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&e->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            e->graph = nullptr;
+            return efail(e, DPD_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+        }
+        e->graph_key = key;
+        e->graph_captures += 1;
+    } else {
+        e->graph_replays += 1;
+    }
+    ENS_TRY(e, cudaGraphLaunch(e->graph, e->stream));
     for (auto &kv : groups) {
         Group &g = kv.second;
         for (const EBox *b : g.init) const_cast<EBox *>(b)->need_init = false;
@@ -615,6 +662,14 @@ dpd_status dpd_ensemble_observables(dpd_ensemble *e, int32_t id, dpd_obs *out)
     out->momentum[0] = h[2];
     out->momentum[1] = h[3];
     out->momentum[2] = h[4];
+    return DPD_OK;
+}
+
+dpd_status dpd_ensemble_graph_stats(dpd_ensemble *e, int64_t *captures, int64_t *replays)
+{
+    if (!e) return efail(e, DPD_ERR_ARG, "null handle");
+    if (captures) *captures = e->graph_captures;
+    if (replays) *replays = e->graph_replays;
     return DPD_OK;
 }
 
@@ -797,6 +852,7 @@ void dpd_ensemble_destroy(dpd_ensemble *e)
         if (e->cls_stream[c]) cudaStreamDestroy(e->cls_stream[c]);
         if (e->join[c]) cudaEventDestroy(e->join[c]);
     }
+    if (e->graph) cudaGraphExecDestroy(e->graph);
     if (e->fork) cudaEventDestroy(e->fork);
     if (e->ev) cudaEventDestroy(e->ev);
     if (e->t0) cudaEventDestroy(e->t0);

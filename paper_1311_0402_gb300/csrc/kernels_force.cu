@@ -125,7 +125,12 @@ __device__ __forceinline__ void add_bonds_body(const SimParams &P, const Ptrs &D
         for (int b = 0; b < kMaxBonds; ++b) {
             const uint32_t other = bp[b];
             if (other == kNone) break;
-            const float4 pj = pos[D.idx_of_pid[other]];
+            const uint32_t jb = kChecked && other >= (uint32_t)P.n ? kNone : D.idx_of_pid[other];
+            if (kChecked && jb >= (uint32_t)P.n) {
+                atomicOr(&D.ctl->err, kErrBadIndex);
+                break;
+            }
+            const float4 pj = pos[jb];
             const float dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
             const float dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
             const float dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
@@ -272,7 +277,7 @@ template <bool ONE_SPECIES, int SMODE, bool WRAP, bool N3, bool VIR>
 __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__restrict__ pos,
                                            const float4 *__restrict__ vel, const uint32_t *__restrict__ list,
                                            uint32_t nent, int lane, WarpSmem &w, const float *a_tab, float4 *facc,
-                                           float &vir)
+                                           float &vir, uint32_t owners, bool &bad)
 {
     const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -362,6 +367,10 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
     // inside r_c, evaluate a full batch
     auto candidate = [&](bool act, uint32_t e, float4 pj) {
         const uint32_t own = e >> kOwnerShift;
+        if (kChecked && act && ((e & kIndexMask) >= (uint32_t)P.n || own >= owners)) {
+            bad = true;
+            act = false;
+        }
         const float3 d = pair_delta<WRAP>(P, pj, w.pi[own]);
         const float d2 = dist2_rn(d.x, d.y, d.z);
         // bitwise & keeps the test branch-free (no short-circuit evaluation)
@@ -384,12 +393,18 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
     // each candidate's position one ahead.  Past the end a lane reads entry 0
     // (owner 0, particle 0), a valid address that the act flag discards.
     auto entry = [&](uint32_t k) -> uint32_t { return k < nent ? __ldg(list + k) : 0u; };
+    // (the checked build clamps the prefetch index into range; the candidate
+    // test then rejects the entry)
+    auto at = [&](uint32_t e) -> uint32_t {
+        const uint32_t j = e & kIndexMask;
+        return (kChecked && j >= (uint32_t)P.n) ? 0u : j;
+    };
     const uint32_t l = (uint32_t)lane;
     uint32_t e0 = entry(l), e1 = entry(32u + l), e2 = entry(64u + l), e3 = entry(96u + l);
-    float4 pc = __ldg(pos + (e0 & kIndexMask));
+    float4 pc = __ldg(pos + at(e0));
     for (uint32_t base = 0; base < nent; base += 32u) {
         const uint32_t e4 = entry(base + 128u + l);
-        const float4 pn = __ldg(pos + (e1 & kIndexMask));
+        const float4 pn = __ldg(pos + at(e1));
         candidate(base + l < nent, e0, pc);
         e0 = e1;
         e1 = e2;
@@ -461,10 +476,12 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
     __syncwarp();
     const uint32_t *__restrict__ list = D.nbr + (size_t)gid * P.gcap;
     float vir = 0.0f;
+    bool bad = false;
     if (all_interior)
-        warp_pairs<ONE_SPECIES, SMODE, false, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir);
+        warp_pairs<ONE_SPECIES, SMODE, false, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir, owners, bad);
     else
-        warp_pairs<ONE_SPECIES, SMODE, true, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir);
+        warp_pairs<ONE_SPECIES, SMODE, true, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir, owners, bad);
+    if (kChecked && __any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(&ctl->err, kErrBadIndex);
     float fx = w.acc[0][lane], fy = w.acc[1][lane], fz = w.acc[2][lane];
 
     if (N3) {
@@ -477,6 +494,99 @@ __global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, in
         if (VIR) block_sum_double(vir, D.vir_part + blockIdx.x);
         return;
     }
+    bool moved = false;
+    if (valid)
+        moved = force_epilogue<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout,
+                                            VIR ? &vir : nullptr);
+    if (VIR) block_sum_double(vir, D.vir_part + blockIdx.x);
+    if (MODE != kForceEval) finish_block(ctl, moved);
+}
+
+// Row layout (list_layout 1): the paper's force evaluation.  One thread per
+// particle walks its row of the transposed table -- entry k of particle
+// 32 g + l sits at row 32 g + (k mod 32), entry 32 (k div 32) + l, so the
+// warp reads each entry index with one coalesced load -- and evaluates every
+// pair inside r_c in its own branch, summing its force in registers in row
+// order (full lists: every pair by both particles, no atomics).  The joined
+// rows list each particle's core pairs first, the ones most likely to be
+// inside r_c, so the warp's threads tend to take the branch together early
+// in the walk.  The epilogue is the deterministic mode's.
+template <bool ONE_SPECIES, int SMODE, bool WRAP, bool VIR>
+__device__ __forceinline__ void row_pairs(const SimParams &P, const Ptrs &D, const float4 *__restrict__ pos,
+                                          const float4 *__restrict__ vel, float4 pi, float4 vi, uint32_t len,
+                                          uint32_t maxlen, size_t row0, int lane, const float *a_tab, float &fx,
+                                          float &fy, float &fz, float &vir, bool &bad)
+{
+    const uint32_t key[4] = {P.key[0], P.key[1], P.key[2], P.key[3]};
+    const size_t cap = (size_t)P.cap;
+    const uint32_t *__restrict__ nbr = D.nbr;
+    for (uint32_t k = 0; k < maxlen; ++k) {
+        if (k < len) {
+            const uint32_t j = __ldg(nbr + (row0 + (k & 31u)) * cap + (k & ~31u) + (uint32_t)lane);
+            if (j >= (uint32_t)P.n) {  // reported, the access skipped
+                bad = true;
+                continue;
+            }
+            const float4 pj = __ldg(pos + j);
+            const float3 d = pair_delta<WRAP>(P, pj, pi);
+            const float d2 = dist2_rn(d.x, d.y, d.z);
+            if (d2 < P.rc2 && d2 > 0.0f) {
+                const float4 vj = __ldg(vel + j);
+                const float inv_r = rsqrtf(d2);
+                const float r = d2 * inv_r;
+                const float wgt = fmaxf(fmaf(-r, P.inv_rc, 1.0f), 0.0f);
+                const float wR = weight_R<SMODE>(wgt, P.s);
+                const float ev = -((d.x * (vi.x - vj.x) + d.y * (vi.y - vj.y)) + d.z * (vi.z - vj.z)) * inv_r;
+                uint32_t A, B;
+                pair_hash(__float_as_uint(vi.w), __float_as_uint(vj.w), key, A, B);
+                const float xi = gauss_from_hash(A, B);
+                const float a = ONE_SPECIES ? P.a[0] : a_tab[__float_as_int(pi.w) * P.n_species + __float_as_int(pj.w)];
+                const float F = fmaf(a, wgt, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
+                if (VIR) vir = fmaf(0.5f, a * wgt * r, vir);
+                const float sc = -F * inv_r;
+                fx = fmaf(sc, d.x, fx);
+                fy = fmaf(sc, d.y, fy);
+                fz = fmaf(sc, d.z, fz);
+            }
+        }
+    }
+}
+
+template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF, bool VIR>
+__global__ void __launch_bounds__(kForceThreads) k_force_rows(SimParams P, Ptrs D, int out_fout)
+{
+    __shared__ float a_tab[kMaxSpecies * kMaxSpecies];
+    if (!ONE_SPECIES) {
+        for (int k = threadIdx.x; k < P.n_species * P.n_species; k += blockDim.x) a_tab[k] = P.a[k];
+        __syncthreads();
+    }
+    DevCtl *ctl = D.ctl;
+    const uint32_t par = ctl->parity;
+    const uint32_t opar = ctl->oparity;
+    const unsigned long long step0 = ctl->step;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < P.n;
+    const float4 *__restrict__ pos = D.pos[par];
+    const float4 *__restrict__ vel = D.vel[par];
+    const float4 pi = valid ? pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 vi = valid ? vel[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t len = valid ? min(D.rowcnt[i], (uint32_t)P.cap) : 0u;
+    const uint32_t maxlen = __reduce_max_sync(0xFFFFFFFFu, len);
+    const size_t row0 = (size_t)(i - lane);
+    const bool interior = !valid || (pi.x >= P.wrap_margin && pi.x <= P.L[0] - P.wrap_margin &&
+                                     pi.y >= P.wrap_margin && pi.y <= P.L[1] - P.wrap_margin &&
+                                     pi.z >= P.wrap_margin && pi.z <= P.L[2] - P.wrap_margin);
+    const bool all_interior = __all_sync(0xFFFFFFFFu, interior) && P.wrap_margin > 0.0f;
+    float fx = 0.f, fy = 0.f, fz = 0.f, vir = 0.f;
+    bool bad = false;
+    if (all_interior)
+        row_pairs<ONE_SPECIES, SMODE, false, VIR>(P, D, pos, vel, pi, vi, len, maxlen, row0, lane, a_tab, fx, fy, fz,
+                                                  vir, bad);
+    else
+        row_pairs<ONE_SPECIES, SMODE, true, VIR>(P, D, pos, vel, pi, vi, len, maxlen, row0, lane, a_tab, fx, fy, fz,
+                                                 vir, bad);
+    if (bad) atomicOr(&ctl->err, kErrBadIndex);
     bool moved = false;
     if (valid)
         moved = force_epilogue<MODE, LHALF>(P, D, ctl, i, pi, vi, fx, fy, fz, par, opar, step0, out_fout,
@@ -519,6 +629,16 @@ constexpr int kMaxDynSmem = 160 * 1024;  // largest staging buffer the brick bui
 template <bool ONE, int MODE, bool LH, bool N3, bool VIR>
 cudaError_t launch_force_v(const SimParams &P, const Ptrs &D, int of, cudaStream_t s)
 {
+    if (!N3 && P.list_layout == 1) {
+        const int gr = (P.n + kForceThreads - 1) / kForceThreads;
+        switch (P.s_mode) {
+        case 1: k_force_rows<ONE, 1, MODE, LH, VIR><<<gr, kForceThreads, 0, s>>>(P, D, of); break;
+        case 2: k_force_rows<ONE, 2, MODE, LH, VIR><<<gr, kForceThreads, 0, s>>>(P, D, of); break;
+        case 3: k_force_rows<ONE, 3, MODE, LH, VIR><<<gr, kForceThreads, 0, s>>>(P, D, of); break;
+        default: k_force_rows<ONE, 0, MODE, LH, VIR><<<gr, kForceThreads, 0, s>>>(P, D, of); break;
+        }
+        return cudaGetLastError();
+    }
     const int g = (P.ngroups + kForceWarps - 1) / kForceWarps;
     switch (P.s_mode) {
     case 1: k_force<ONE, 1, MODE, LH, N3, VIR><<<g, kForceThreads, 0, s>>>(P, D, of); break;

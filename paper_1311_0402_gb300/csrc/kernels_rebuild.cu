@@ -207,6 +207,10 @@ __global__ void k_gather(SimParams P, Ptrs D)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < lim; p += gridDim.x * blockDim.x) {
         if (p < P.n) {
             uint32_t i = IDENT ? (uint32_t)p : D.perm[p];
+            if (kChecked && i >= (uint32_t)P.n) {
+                atomicOr(&D.ctl->err, kErrBadIndex);
+                i = (uint32_t)p;
+            }
             float4 x = D.pos[s][i];
             D.pos[t][p] = x;
             D.xref[p] = x;
@@ -373,12 +377,75 @@ __device__ __forceinline__ bool within_list(const SimParams &P, float4 pj, float
     return dist2_rn(dx, dy, dz) < P.rlist2;
 }
 
+template <bool WRAP>
+__device__ __forceinline__ float pair_d2(const SimParams &P, float4 pj, float4 pi)
+{
+    float dx, dy, dz;
+    if (WRAP) {
+        dx = min_image_rn(pj.x, pi.x, P.L[0], P.halfL[0]);
+        dy = min_image_rn(pj.y, pi.y, P.L[1], P.halfL[1]);
+        dz = min_image_rn(pj.z, pi.z, P.L[2], P.halfL[2]);
+    } else {
+        dx = __fsub_rn(pj.x, pi.x);
+        dy = __fsub_rn(pj.y, pi.y);
+        dz = __fsub_rn(pj.z, pi.z);
+    }
+    return dist2_rn(dx, dy, dz);
+}
+
 // Per-warp table of one slot of the candidate sequence: head[l] is the
 // sequence entry (cell) whose first candidate falls on lane l.
 struct CellSeq {
     uint8_t head[32];
-    uint32_t count;  // atomic-append variant: the group's running total
+    uint32_t count;    // atomic-append variant: the group's running total
+    uint32_t rows[32]; // row layout: each owner's counts, core | skin << 16
 };
+
+// Row layout (list_layout 1, the paper's Sec. 3.3): owner io has the row
+// nbr[io * cap, io * cap + cap).  A warp works on one owner at a time; the
+// pairs inside r_c at build time (core) are appended at the front of the row
+// in sequence order, the other pairs inside r_list (skin) at its back in
+// reverse order -- the double insertion, one table and two counters -- and
+// k_rows_join later moves the skin part behind the core part.  Full lists:
+// every pair is listed by both of its particles.
+template <bool WRAP, bool STAGED, int NS>
+__device__ __forceinline__ void owner_pass_rows(const SimParams &P, const float4 *__restrict__ pos,
+                                                const float4 *s_pos, const uint32_t *s_off,
+                                                const float4 (&cand)[kSlots], int t, uint32_t g_own, uint32_t p_lo,
+                                                uint32_t p_hi, uint32_t c0, uint32_t c1, uint32_t first, uint32_t lane,
+                                                uint32_t *nbr, uint32_t cap, uint32_t *rows)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t p = p_lo; p < p_hi; ++p) {
+        const uint32_t io = g_own + p;
+        const float4 pio = STAGED ? s_pos[s_off[t] + p] : pos[io];
+        const uint32_t o = io - first;
+        uint32_t core = rows[o] & 0xFFFFu, skin = rows[o] >> 16;
+        uint32_t *row = nbr + (size_t)io * cap;
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) {
+            const uint32_t k = c0 + 32u * sl + lane;
+            const uint32_t j = __float_as_uint(cand[sl].w);
+            const float d2 = pair_d2<WRAP>(P, cand[sl], pio);
+            const bool cand_ok = (k < c1) & (j != io);
+            const uint32_t m_core = __ballot_sync(0xFFFFFFFFu, cand_ok & (d2 < P.rc2));
+            const uint32_t m_skin = __ballot_sync(0xFFFFFFFFu, cand_ok & (d2 < P.rlist2) & !(d2 < P.rc2));
+            if ((m_core >> lane) & 1u) {
+                const uint32_t q = core + (uint32_t)__popc(m_core & lt);
+                if (q < cap) row[q] = j;
+            }
+            if ((m_skin >> lane) & 1u) {
+                const uint32_t q = skin + (uint32_t)__popc(m_skin & lt);
+                if (q < cap) row[cap - 1u - q] = j;
+            }
+            core += (uint32_t)__popc(m_core);
+            skin += (uint32_t)__popc(m_skin);
+        }
+        __syncwarp();
+        if (lane == 0) rows[o] = min(core, 0xFFFFu) | (min(skin, 0xFFFFu) << 16);
+        __syncwarp();
+    }
+}
 
 // One chunk against the owners [p_lo, p_hi) of cell slot t, kOwnersPerPass
 // owners at a time: every ballot of the pass over the NS live slots first
@@ -456,7 +523,7 @@ __device__ __forceinline__ uint32_t owner_pass(const SimParams &P, const float4 
 // the group list; returns the new running total.  A chunk of kChunk
 // candidates is held in registers, lane l holding entries c0 + 32 s + l;
 // every owner of the cell tests against the same registers (owner_pass).
-template <bool WRAP, bool STAGED, bool HALF, bool ATOMIC>
+template <bool WRAP, bool STAGED, bool HALF, bool ATOMIC, bool ROWS = false>
 __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 *__restrict__ pos,
                                                const float4 *s_pos, const uint32_t *s_off, const uint32_t *s_gstart,
                                                const uint32_t *s_cnt, CellSeq &w, int t, uint32_t p_lo, uint32_t p_hi,
@@ -520,6 +587,18 @@ __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 
             }
         }
         const uint32_t ns = (c1 - c0 + 31u) / 32u;  // live slots of this chunk
+        if (ROWS) {
+            // list = the whole table, gcap = the row capacity
+            if (ns == 4u)
+                owner_pass_rows<WRAP, STAGED, 4>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
+            else if (ns == 3u)
+                owner_pass_rows<WRAP, STAGED, 3>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
+            else if (ns == 2u)
+                owner_pass_rows<WRAP, STAGED, 2>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
+            else
+                owner_pass_rows<WRAP, STAGED, 1>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
+            continue;
+        }
         if (ns == 4u)
             total = owner_pass<WRAP, STAGED, HALF, 4, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
         else if (ns == 3u)
@@ -532,7 +611,7 @@ __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 
     return total;
 }
 
-template <bool ATOMIC>
+template <bool ATOMIC, bool ROWS>
 __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
@@ -580,10 +659,14 @@ __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, 
             inner_lane = grid5 && cx >= 1 && cx <= P.nc[0] - 2 && cy >= 1 && cy <= P.nc[1] - 2 && cz >= 1 &&
                          cz <= P.nc[2] - 2;
         }
-        uint32_t *list = D.nbr + (size_t)(gbase + q) * gcap;
+        uint32_t *list = ROWS ? D.nbr : D.nbr + (size_t)(gbase + q) * gcap;
         uint32_t total = 0;
         if (ATOMIC) {
             if (lane == 0) w.count = 0u;
+            __syncwarp();
+        }
+        if (ROWS) {
+            w.rows[lane] = 0u;
             __syncwarp();
         }
         // the group's particles are sorted by cell: take the cells in turn
@@ -594,7 +677,15 @@ __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, 
             const bool inner = __shfl_sync(0xFFFFFFFFu, inner_lane, (int)l0) != 0;
             const uint32_t p_lo = first + l0 - s_gstart[t];
             const uint32_t p_hi = p_lo + run;
-            if (P.newton3) {
+            if (ROWS) {
+                const uint32_t rcap = (uint32_t)P.cap;
+                if (!local)
+                    build_cell<true, false, false, false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, rcap, 0u);
+                else if (inner)
+                    build_cell<false, true, false, false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, rcap, 0u);
+                else
+                    build_cell<true, true, false, false, true>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, rcap, 0u);
+            } else if (P.newton3) {
                 if (!local)
                     total = build_cell<true, false, true, ATOMIC>(P, pos, s_pos, s_off, s_gstart, s_cnt, w, t, p_lo, p_hi, first, lane, list, gcap, total);
                 else if (inner)
@@ -615,12 +706,82 @@ __global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, 
             __syncwarp();
             total = w.count;
         }
-        if (lane == 0) write_group(D, P, gbase + q, first, owners, total);
+        if (ROWS) {
+            // each owner's counts; a row whose two parts do not fit its
+            // capacity reports an overflow (the list is rebuilt larger)
+            __syncwarp();
+            const uint32_t rc = w.rows[lane];
+            const uint32_t len = (rc & 0xFFFFu) + (rc >> 16);
+            if (lane < owners) {
+                D.rowcnt[first + lane] = rc;
+                if (len > (uint32_t)P.cap) atomicOr(&D.ctl->err, kErrNbrOverflow);
+            }
+            total = __reduce_max_sync(0xFFFFFFFFu, lane < owners ? len : 0u);
+            __syncwarp();
+        } else if (lane == 0) {
+            write_group(D, P, gbase + q, first, owners, total);
+        }
         local_max = total > local_max ? total : local_max;
     }
     // ids of this brick's range that no group took
     for (uint32_t g = gbase + ngrp + threadIdx.x; g < gnext; g += blockDim.x) D.gdesc[g] = make_uint2(0u, 0u);
     if (lane == 0 && local_max) atomicMax(&D.ctl->max_nnb, local_max);
+}
+
+// Row layout: join the two parts of every row (the paper's NeighborListJoin):
+// the skin entries, stored from the row's end backwards, are moved behind the
+// core entries in their insertion order, so a row reads core pairs first and
+// skin pairs after them.  One thread per row: reverse the skin block in
+// place, then copy it down to the end of the core block (copying towards
+// lower addresses in increasing order never overwrites an unread entry).
+__global__ void k_rows_join(SimParams P, Ptrs D)
+{
+    if (!D.ctl->rebuild) return;
+    const uint32_t cap = (uint32_t)P.cap;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+        const uint32_t rc = D.rowcnt[i];
+        uint32_t core = rc & 0xFFFFu, skin = rc >> 16;
+        if (core > cap) core = cap;
+        if (skin > cap - core) skin = cap - core;  // overflowed: reported by the builder
+        uint32_t *row = D.nbr + (size_t)i * cap;
+        for (uint32_t a = cap - skin, b = cap - 1u; a < b; ++a, --b) {
+            const uint32_t x = row[a];
+            row[a] = row[b];
+            row[b] = x;
+        }
+        for (uint32_t k = 0; k < skin; ++k) row[core + k] = row[cap - skin + k];
+        D.rowcnt[i] = core + skin;
+    }
+}
+
+// Row layout: transpose every 32 x 32 tile of the table in place (the paper's
+// local transposition, NeighborListTranspose): rows 32 g .. 32 g + 31 and
+// entries 32 c .. 32 c + 31 swap their roles, so that entry k of particle
+// 32 g + l ends up at row 32 g + (k mod 32), entry 32 (k div 32) + l, and a
+// warp whose lane l walks particle 32 g + l reads each entry index with one
+// coalesced load.  One warp per group of 32 rows, over the tiles its
+// longest row reaches.
+__global__ void k_rows_transpose(SimParams P, Ptrs D)
+{
+    if (!D.ctl->rebuild) return;
+    __shared__ uint32_t tile[kBuildWarps][32][33];
+    const uint32_t cap = (uint32_t)P.cap, lane = threadIdx.x & 31u, wl = threadIdx.x / 32u;
+    const uint32_t ngroups = ((uint32_t)P.n + 31u) / 32u;
+    const uint32_t nwarps = gridDim.x * blockDim.x / 32u;
+    for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) / 32u; g < ngroups; g += nwarps) {
+        const uint32_t i = g * 32u + lane;
+        const uint32_t len = i < (uint32_t)P.n ? D.rowcnt[i] : 0u;
+        const uint32_t ntiles = (__reduce_max_sync(0xFFFFFFFFu, len) + 31u) / 32u;
+        uint32_t *base = D.nbr + (size_t)g * 32u * cap;
+        for (uint32_t c = 0; c < ntiles; ++c) {
+#pragma unroll 8
+            for (uint32_t r = 0; r < 32u; ++r) tile[wl][r][lane] = base[(size_t)r * cap + 32u * c + lane];
+            __syncwarp();
+#pragma unroll 8
+            for (uint32_t r = 0; r < 32u; ++r) base[(size_t)r * cap + 32u * c + lane] = tile[wl][lane][r];
+            __syncwarp();
+        }
+    }
 }
 
 // Failure-detection probe: the bounded mbarrier wait of the brick staging,
@@ -651,9 +812,12 @@ int scan_blocks_for(int ncell) { return (ncell + kScanTile - 1) / kScanTile; }
 
 cudaError_t init_build_attributes(int max_dyn_smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_nbuild_brick<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_nbuild_brick<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    cudaError_t e = cudaFuncSetAttribute(k_nbuild_brick<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_nbuild_brick<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_nbuild_brick<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem);
+    return e;
 }
 
 cudaError_t launch_index(const SimParams &P, const Ptrs &D, cudaStream_t s)
@@ -682,10 +846,15 @@ cudaError_t launch_rebuild(const SimParams &P, const Ptrs &D, cudaStream_t s, in
     k_commit<<<1, 1, 0, s>>>(D);
     if (P.use_bricks) {
         const size_t smem = sizeof(float4) * (size_t)P.brick_cap;
-        if (P.list_builder == 1)
-            k_nbuild_brick<true><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
-        else
-            k_nbuild_brick<false><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
+        if (P.list_layout == 1) {
+            k_nbuild_brick<false, true><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
+            k_rows_join<<<g, kThreads, 0, s>>>(P, D);
+            k_rows_transpose<<<grid_for((P.n + 31) / 32 * 32), kBuildThreads, 0, s>>>(P, D);
+        } else if (P.list_builder == 1) {
+            k_nbuild_brick<true, false><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
+        } else {
+            k_nbuild_brick<false, false><<<P.nbricks, kBuildThreads, smem, s>>>(P, D);
+        }
     } else if (P.no_reorder) {
         k_nbuild<true><<<g, kThreads, 0, s>>>(P, D);
     } else {

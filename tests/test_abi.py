@@ -34,6 +34,14 @@ def test_library_builds_and_exports_every_declared_symbol():
     assert set(dpd.EXPORTS) == declared
 
 
+def test_checked_library_exports_the_same_symbols():
+    path = dbuild.build(checked=True)
+    assert os.path.basename(path) == "libdpd_checked.so"
+    L = ctypes.CDLL(path)
+    missing = [n for n in sorted(_declared()) if not hasattr(L, n)]
+    assert not missing, missing
+
+
 def test_argument_errors_need_no_gpu():
     dbuild.build()
     # validation happens before any CUDA call

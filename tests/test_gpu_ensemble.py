@@ -14,7 +14,7 @@ import pytest
 import oracle
 import paper_1311_0402_gb300 as dpd
 import workloads
-from gpu_util import force_error, need_gpu
+from gpu_util import agree, force_error, need_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -143,7 +143,7 @@ def test_thermodynamics_match_the_engine():
     ens.step(500)
     sim.step(500)
     te, pe, ts, ps = [], [], [], []
-    for _ in range(60):
+    for _ in range(200):
         ens.step(20)
         sim.step(20)
         ens.sync()
@@ -151,8 +151,10 @@ def test_thermodynamics_match_the_engine():
         te.append(a["temperature"]); pe.append(a["pressure"])
         ts.append(b["temperature"]); ps.append(b["pressure"])
     assert abs(np.mean(te) - 1.0) < 0.03 and 22.5 < np.mean(pe) < 25.0
-    assert abs(np.mean(te) - np.mean(ts)) < 0.015
-    assert abs(np.mean(pe) - np.mean(ps)) < 0.01 * np.mean(ps)
+    ok, why = agree(te, ts, 0.01)
+    assert ok, why
+    ok, why = agree(pe, ps, 0.01 * np.mean(ps))
+    assert ok, why
     assert abs(ens.observables(i)["momentum"]).max() < 1e-2
     ens.close()
     sim.close()
@@ -320,7 +322,7 @@ def test_newton3_trajectory_and_thermodynamics():
     ens.step(500)
     det.step(500)
     t3, p3, td, pd = [], [], [], []
-    for _ in range(50):
+    for _ in range(200):
         ens.step(20)
         det.step(20)
         ens.sync()
@@ -328,8 +330,42 @@ def test_newton3_trajectory_and_thermodynamics():
         a, b = ens.observables(i), det.observables(j)
         t3.append(a["temperature"]); p3.append(a["pressure"])
         td.append(b["temperature"]); pd.append(b["pressure"])
-    assert abs(np.mean(t3) - np.mean(td)) < 0.015
-    assert abs(np.mean(p3) - np.mean(pd)) < 0.01 * np.mean(pd)
+    ok, why = agree(t3, td, 0.01)
+    assert ok, why
+    ok, why = agree(p3, pd, 0.01 * np.mean(pd))
+    assert ok, why
     assert abs(ens.observables(i)["momentum"]).max() < 1e-2
     ens.close()
     det.close()
+
+
+def test_chunk_launches_replay_a_captured_graph():
+    """Step calls with the same boxes per class replay one captured CUDA graph
+    (the step counts travel in the device descriptors), and the trajectory is
+    the same bit for bit as with a fresh capture for every call (another
+    ensemble whose structure changes between calls)."""
+    box, x, v = _fluid(7, 141)
+    a = dpd.Ensemble()
+    i = _add(a, box, x, v)
+    for k in (5, 7, 5, 9):
+        a.step(k)
+    a.sync()
+    cap, rep = a.graph_stats()
+    # the first call also computes the initial force (its own structure)
+    assert cap == 2 and rep == 2, (cap, rep)
+    b = dpd.Ensemble()
+    j = _add(b, box, x, v)
+    box2, x2, v2 = _fluid(6, 142)
+    for n, k in enumerate((5, 7, 5, 9)):
+        # a second box added and removed between calls changes the structure
+        extra = _add(b, box2, x2, v2) if n % 2 == 0 else None
+        b.step(k, ids=[j] if extra is None else [j, extra])
+        b.sync()
+        if extra is not None:
+            b.remove(extra)
+    xa, va, sa = a.state(i)
+    xb, vb, sb = b.state(j)
+    assert sa == sb == 26
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    a.close()
+    b.close()

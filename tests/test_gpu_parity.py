@@ -203,7 +203,71 @@ def test_no_reorder_ablation_same_physics(deterministic):
     assert force_error(g.forces(), fo)[0] < FORCE_TOL
     g.step(25)
     assert g.info()["rebuilds"] > 1
+    # forces from the list the run last built; the set after a rebuild at the
+    # current positions (the list of a run dates from its last rebuild)
     x32, v32, step = g.state()
-    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, cfg["box"], cfg["rc"] + 0.3))
     fo, _ = o.forces(x32, v32, step=step)
     assert force_error(g.forces(), fo)[0] < FORCE_TOL
+    g.build_neighbors()
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, cfg["box"], cfg["rc"] + 0.3))
+
+
+@pytest.mark.parametrize("name", ["fluid_small", "poiseuille_small", "amphiphile_small", "dense_small"])
+def test_row_layout_matches_oracle(name):
+    """The paper's list layout (Sec. 3.3): one row per particle with the core
+    pairs inserted from the front and the skin pairs from the back, the two
+    parts joined, each 32 x 32 tile transposed in place, and one thread per
+    particle in the pair force.  The same pairs as the oracle's FP32
+    predicate, the same forces within the tolerance, and after steps that
+    rebuild the list (regrowing the rows in the dense box) still both."""
+    st, cfg, box, bonds = _workload(name)
+    g, o = make_pair(cfg, box=box, bonds=bonds, list_layout=1)
+    g.set_state(st["x"], st["v"], st["species"], step=11)
+    if bonds is not None:
+        g.set_bonds(bonds, cfg["k_bond"], cfg["r0_bond"])
+    x32, v32, step = g.state()
+    rl = cfg["rc"] + 0.3
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, box, rl))
+    fo, _ = o.forces(x32, v32, species=st["species"], step=step)
+    err, rms = force_error(g.forces(), fo)
+    assert err < FORCE_TOL, (err, rms)
+    g.step(20)
+    assert g.info()["rebuilds"] > 1
+    # the forces use the list the run last built (a superset of the pairs
+    # inside r_c at the current positions); the set is compared after a
+    # rebuild at the current positions
+    x32, v32, step = g.state()
+    fo, _ = o.forces(x32, v32, species=st["species"], step=step)
+    err, rms = force_error(g.forces(), fo)
+    assert err < FORCE_TOL, (err, rms)
+    g.build_neighbors()
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, box, rl))
+    g.close()
+
+
+def test_row_layout_trajectory_equals_packed_deterministic():
+    """Both layouts evaluate every pair from both particles and sum each force
+    in a fixed order; two row-layout runs of 30 steps are bit-identical, and
+    over 5 steps the two layouts agree to rounding (their summation orders
+    differ)."""
+    st = workloads.make("fluid_small")
+    cfg = st["cfg"]
+    runs = []
+    for layout, nsteps in ((1, 30), (1, 30), (1, 5), (0, 5)):
+        g, _ = make_pair(cfg, deterministic=1, list_layout=layout)
+        g.set_state(st["x"], st["v"])
+        g.step(nsteps)
+        runs.append(g.state())
+        g.close()
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    dx = runs[2][0] - runs[3][0]
+    dx -= np.asarray(cfg["box"]) * np.round(dx / np.asarray(cfg["box"]))
+    assert np.abs(dx).max() < 1e-5
+    assert np.abs(runs[2][1] - runs[3][1]).max() < 1e-3
+
+
+def test_row_layout_needs_three_cells_per_axis():
+    box = (3.2, 3.5, 2.9)  # 2 cells per axis
+    with pytest.raises(dpd.DPDError) as e:
+        dpd.Sim(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, list_layout=1)
+    assert e.value.status == 1
