@@ -438,8 +438,13 @@ __device__ __forceinline__ void block_sum_double(float x, double *out)
 // VIR: also the virial of this evaluation (conservative pairs + bonds), one
 // partial per block into D.vir_part -- for the evaluations that close a call,
 // whose positions are the state the observables describe.
+// 12 resident blocks per SM (48 warps) caps the kernel at 40 registers: the
+// walk's scattered gathers need the extra warps to hide their latency
+// (measured on the 3M fluid: 0.311 ms per launch against 0.338 ms at the
+// compiler's 47 registers and 10 blocks; 32 registers spill and take 0.474).
+constexpr int kForceMinBlocks = 12;
 template <bool ONE_SPECIES, int SMODE, int MODE, bool LHALF, bool N3, bool VIR>
-__global__ void __launch_bounds__(kForceThreads) k_force(SimParams P, Ptrs D, int out_fout)
+__global__ void __launch_bounds__(kForceThreads, kForceMinBlocks) k_force(SimParams P, Ptrs D, int out_fout)
 {
     constexpr int W = kForceThreads / 32;
     __shared__ WarpSmem s_w[W];
