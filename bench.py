@@ -328,7 +328,8 @@ def run_serving(args):
                           b["steps"], seed=b["seed"], skin=b["skin"])
 
     # (2) saturated: everything queued at once, every box on its own handle;
-    # then the same with the boxes that fit routed to the ensemble kernel
+    # then the same with adaptive routing (a box that fits the ensemble kernel
+    # goes there while every handle slot is busy)
     def saturated(ensemble):
         srv = dpd.Server(max_active=args.serve_active, chunk_steps=100, ensemble=ensemble)
         t0 = srv.now()
@@ -338,7 +339,7 @@ def run_serving(args):
         return max(r["t_done"] for r in res) - t0, sum(1 for r in res if r["status"] != 0)
 
     t_sat, bad = saturated(0)
-    t_sat_e, bad_e = saturated(1)
+    t_sat_e, bad_e = saturated(2)
     bad += bad_e
     # (3) Poisson arrivals at 1.2x the one-box-at-a-time capacity
     rate = 1.2 * len(boxes) / t_seq
@@ -361,7 +362,7 @@ def run_serving(args):
                 "p50_s": float(np.percentile(ttc, 50)), "p99_s": float(np.percentile(ttc, 99)),
                 "arrival": "Poisson, 1.2x the one-box-at-a-time capacity"}, sum(1 for r in res if r["status"] != 0)
 
-    pois, b1 = poisson(1)
+    pois, b1 = poisson(2)
     pois_plain, b2 = poisson(0)
     bad += b1 + b2
     n_ens = sum(1 for b in boxes if dpd.dpd_ensemble_fits(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"],
@@ -380,10 +381,11 @@ def run_serving(args):
                       "routing": "every box on its own handle (the serving loop's default)"},
         "saturated_ensemble_routing": {"value": total / t_sat_e, "unit": UNIT, "wall_s": t_sat_e,
                                        "vs_one_box_at_a_time": t_seq / t_sat_e, "max_active": args.serve_active,
-                                       "routing": "boxes that fit run in the ensemble kernel, the others on "
-                                                  "their own handles"},
+                                       "routing": "adaptive: a box that fits the ensemble kernel runs there "
+                                                  "while every handle slot is busy, else on its own handle"},
         "poisson": dict(pois_plain, routing="every box on its own handle (the serving loop's default)"),
-        "poisson_ensemble_routing": dict(pois, routing="boxes that fit run in the ensemble kernel"),
+        "poisson_ensemble_routing": dict(pois, routing="adaptive: a box that fits the ensemble kernel runs there "
+                                                       "while every handle slot is busy, else on its own handle"),
     }
 
 

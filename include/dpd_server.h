@@ -48,7 +48,12 @@ typedef struct {
                                   about 4,000 particles or fewer, each side >= 3 rc) run
                                   there instead, all of them advanced together by one
                                   launch per size class and chunk, driven by one more
-                                  worker thread; 0 (default): every box on its own handle */
+                                  worker thread; 2: a box that fits goes to the ensemble
+                                  only when, at its admission, every one of the
+                                  max_active handle slots is busy (otherwise it runs on a
+                                  handle: the ensemble adds throughput under load without
+                                  costing per-box latency when slots are free); 0
+                                  (default): every box on its own handle */
     int32_t ensemble_slots;    /* boxes resident in the ensemble at once (default 1024) */
 } dpd_server_options;
 
@@ -78,6 +83,8 @@ typedef struct {
     double t_admit;            /* admitted: taken from the queue (device memory reserved) */
     double t_done;             /* final state read back */
     dpd_obs obs;               /* observables of the final state */
+    int32_t engine;            /* 0: the box ran on its own handle (dpd.h); 1: in the
+                                  ensemble kernel (dpd_ensemble.h) */
 } dpd_result;
 
 /* Results of boxes run by the ensemble kernel are bit-identical to the same box

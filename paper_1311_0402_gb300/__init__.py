@@ -120,6 +120,7 @@ class dpd_result(ctypes.Structure):
         ("t_admit", ctypes.c_double),
         ("t_done", ctypes.c_double),
         ("obs", dpd_obs),
+        ("engine", ctypes.c_int32),
     ]
 
 
@@ -577,7 +578,7 @@ class Server:
                  graph_steps=8, lam=0.5, conditional_rebuild=0, workers=4, ensemble=0, ensemble_slots=1024):
         o = dpd_server_options()
         lib().dpd_server_default_options(ctypes.byref(o))
-        o.ensemble = 1 if ensemble else 0
+        o.ensemble = int(ensemble)  # 0 off, 1 every box that fits, 2 only while the handle slots are full
         o.ensemble_slots = ensemble_slots
         o.max_active = max_active
         o.workers = workers
@@ -625,7 +626,7 @@ class Server:
         self._n.pop(ticket, None)
         o = res.obs
         out = dict(ticket=res.ticket, status=res.status, n=res.n, steps=res.steps, t_submit=res.t_submit,
-                   t_admit=res.t_admit, t_done=res.t_done,
+                   t_admit=res.t_admit, t_done=res.t_done, engine=res.engine,
                    obs=dict(step=o.step, n=o.n, kinetic=o.kinetic, temperature=o.temperature, virial=o.virial,
                             pressure=o.pressure, momentum=np.array(list(o.momentum))))
         if state:

@@ -43,7 +43,9 @@ struct Job {
     uint64_t steps = 0;
     double skin = 0;        // 0: the server's box_options.skin
     double est_bytes = 0;
-    bool ens = false;       // runs in the ensemble kernel
+    double est_ens_bytes = 0;
+    bool ens = false;       // routed to the ensemble kernel at submission (ensemble = 1)
+    bool ens_fit = false;   // fits the ensemble kernel (ensemble = 2 decides at admission)
     double t_submit = 0;
     double t_admit = 0;     // stamped under the server's lock when taken from the queue
 };
@@ -116,6 +118,7 @@ struct dpd_server {
     std::map<uint64_t, Done> done;
     std::map<uint64_t, bool> known;  // submitted and not yet collected
     int64_t running = 0;
+    int64_t handle_active = 0;  // boxes admitted to their own handles and not finished
     double mem_used = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -163,6 +166,7 @@ void finish(dpd_server *S, Slot &sl, dpd_status st, const std::string &msg)
         std::lock_guard<std::mutex> lk(S->m);
         S->done[sl.job.ticket] = std::move(d);
         S->running -= 1;
+        S->handle_active -= 1;
         S->mem_used -= sl.job.est_bytes;
         if (!m2.empty()) S->err = "ticket " + std::to_string(sl.job.ticket) + ": " + m2;
     }
@@ -218,6 +222,7 @@ void worker_loop(dpd_server *S, int slots)
                     if (S->mem_used + it->est_bytes <= S->budget) {
                         S->mem_used += it->est_bytes;
                         S->running += 1;
+                        S->handle_active += 1;
                         it->t_admit = S->now();
                         admit.push_back(std::move(*it));
                         it = S->pending.erase(it);
@@ -313,6 +318,7 @@ void ensemble_loop(dpd_server *S)
         d.res.steps = ej.job.steps;
         d.res.t_submit = ej.job.t_submit;
         d.res.t_admit = ej.job.t_admit;
+        d.res.engine = 1;
         std::string m2 = msg;
         if (st == DPD_OK && ej.id >= 0) {
             d.x.resize(3 * (size_t)ej.job.n);
@@ -341,18 +347,24 @@ void ensemble_loop(dpd_server *S)
         bool stopping = false;
         {
             std::unique_lock<std::mutex> lk(S->m);
+            // adaptive routing (ensemble = 2): a box that fits is taken here
+            // only while every handle slot is busy, so under light load the
+            // boxes keep the handles' per-box latency
+            const bool handles_full = S->handle_active >= S->opt.max_active;
+            auto mine = [&](const Job &j) { return j.ens || (S->opt.ensemble == 2 && j.ens_fit && handles_full); };
             bool any = false;
-            for (const Job &j : S->pending) any = any || j.ens;
+            for (const Job &j : S->pending) any = any || mine(j);
             if (active.empty() && !any && !S->stop) S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
             stopping = S->stop;
             if (!stopping) {
                 int looked = 0;
                 for (auto it = S->pending.begin();
                      it != S->pending.end() && (int)(active.size() + admit.size()) < slots && looked < 16;) {
-                    if (!it->ens) {
+                    if (!mine(*it)) {
                         ++it;
                         continue;
                     }
+                    if (!it->ens) it->est_bytes = it->est_ens_bytes;  // taken by adaptive routing
                     if (S->mem_used + it->est_bytes <= S->budget) {
                         S->mem_used += it->est_bytes;
                         S->running += 1;
@@ -464,7 +476,7 @@ dpd_status dpd_server_create(const dpd_server_options *o, dpd_server **out)
     dpd_server_options opt;
     if (o) opt = *o; else dpd_server_default_options(&opt);
     if (opt.max_active < 1 || opt.workers < 1 || opt.chunk_steps < 1 || !(opt.mem_budget_bytes >= 0.0) ||
-        opt.ensemble < 0 || opt.ensemble > 1 || (opt.ensemble && opt.ensemble_slots < 1))
+        opt.ensemble < 0 || opt.ensemble > 2 || (opt.ensemble && opt.ensemble_slots < 1))
         return DPD_ERR_ARG;
     dpd_server *S = new dpd_server();
     S->opt = opt;
@@ -515,9 +527,11 @@ dpd_status dpd_server_submit(dpd_server *S, const dpd_request *r, uint64_t *tick
     j.skin = r->skin;
     if (S->opt.ensemble) {
         const dpd_box_params p = box_params_of(j, S->opt.box_options);
-        j.ens = dpd_ensemble_fits(&p, j.n) != 0;
+        j.ens_fit = dpd_ensemble_fits(&p, j.n) != 0;
+        j.ens = j.ens_fit && S->opt.ensemble == 1;
     }
-    j.est_bytes = j.ens ? estimate_ensemble_bytes(j) : estimate_bytes(j, S->opt.box_options);
+    j.est_ens_bytes = estimate_ensemble_bytes(j);
+    j.est_bytes = j.ens ? j.est_ens_bytes : estimate_bytes(j, S->opt.box_options);
     if (j.est_bytes > S->budget) return fail_s(S, DPD_ERR_OOM, "box needs more device memory than the budget");
     {
         std::lock_guard<std::mutex> lk(S->m);

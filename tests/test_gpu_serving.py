@@ -174,3 +174,41 @@ def test_ensemble_routing_alone_and_in_the_mix():
         assert step == b["steps"]
         assert np.array_equal(r["x"], x) and np.array_equal(r["v"], v), "box L=%g" % b["box"][0]
         assert r["obs"]["temperature"] == ob["temperature"] and r["obs"]["virial"] == ob["virial"]
+
+
+def test_adaptive_ensemble_routing():
+    """ensemble = 2: a box that fits the ensemble kernel runs there only when,
+    at its admission, every handle slot is busy.  With one slot and a queue of
+    small boxes some go each way; each result is bit-identical to the same box
+    run alone on the path it took (deterministic mode).  A box submitted to an
+    idle server runs on a handle."""
+    need_gpu()
+    boxes = _boxes(8, seed=21, L_range=(6, 8), steps_range=(300, 400))
+    srv = dpd.Server(max_active=1, chunk_steps=CHUNK, deterministic=1, ensemble=2)
+    tickets = [srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
+                          b["steps"], seed=b["seed"]) for b in boxes]
+    res = [srv.wait(t, timeout_s=300.0) for t in tickets]
+    engines = [r["engine"] for r in res]
+    assert 0 in engines and 1 in engines, engines
+    for b, r in zip(boxes, res):
+        assert r["status"] == 0 and r["obs"]["step"] == b["steps"]
+        if r["engine"] == 1:
+            ens = dpd.Ensemble()
+            i = ens.add(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"],
+                        seed=b["seed"])
+            left = b["steps"]
+            while left > 0:
+                ens.step(min(CHUNK, left))
+                left -= min(CHUNK, left)
+            ens.sync()
+            x, v, step = ens.state(i)
+            ens.close()
+        else:
+            x, v, step, _ = _alone(b, 1)
+        assert np.array_equal(r["x"], x) and np.array_equal(r["v"], v)
+    # light load: one box into an idle server takes a handle
+    b = boxes[0]
+    t = srv.submit(b["box"], b["a"], b["gamma"], b["kT"], b["rc"], b["s"], b["dt"], b["x"], b["v"], b["steps"],
+                   seed=b["seed"])
+    assert srv.wait(t, timeout_s=300.0)["engine"] == 0
+    srv.close()
