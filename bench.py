@@ -48,6 +48,9 @@ ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 # algorithmic lane-ops per unique interacting pair (distance, weights,
 # TEA-4 pair hash, Box-Muller, force, accumulation on both particles)
 OPS_PER_PAIR = 100.0
+# per particle and step: the half kick, drift, wrap, full kick and
+# displacement test of the lambda form of velocity Verlet
+OPS_INTEGRATE = 25.0
 PROFILES = os.path.join(ROOT, "profiles")
 
 
@@ -617,6 +620,12 @@ def main():
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and max clock)"}
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (152 * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    # the whole step against the same peak: the pair work plus the integrator's
+    # lane-ops per particle, over the measured time per step (rebuilds included)
+    step_ops = n * (pairs_per_particle * OPS_PER_PAIR + OPS_INTEGRATE)
+    step_achieved = step_ops / (max_ms / 1e3 / args.steps) / 1e12
+    roofline["whole_step"] = {"achieved": step_achieved, "frac": step_achieved / ALU_PEAK_TOPS,
+                              "lane_ops_per_particle_step": step_ops / n, "unit": "TOP/s"}
 
     # end to end through the public API with host buffers (pinned)
     e2e_steps = max(1, min(args.e2e_steps, args.steps))

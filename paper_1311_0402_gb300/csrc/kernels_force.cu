@@ -268,8 +268,8 @@ __device__ __forceinline__ void red_add_f4(float4 *p, float x, float y, float z)
 struct WarpSmem {
     float4 pi[32];
     float4 vi[32];
-    float4 q[kQueue];      // (d, j)
-    uint8_t qo[kQueue];    // owner lane | partner species << 5
+    float4 q[kQueue];      // (d, list entry: owner lane << kOwnerShift | j)
+    uint8_t qo[kQueue];    // partner species (several species only)
     float acc[3][32];
 };
 
@@ -290,11 +290,13 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
         uint32_t owner = 32u + (uint32_t)lane;  // distinct dummy owners for idle lanes
         if (act) {
             const uint32_t slot = (head + (uint32_t)lane) & (kQueue - 1);
-            const float4 q = w.q[slot];  // (d, j)
-            const uint32_t qo = w.qo[slot];
-            owner = qo & 31u;
+            const float4 q = w.q[slot];  // (d, list entry)
+            const uint32_t ent = __float_as_uint(q.w);
+            const uint32_t qo = ONE_SPECIES ? 0u : w.qo[slot];
+            owner = ent >> kOwnerShift;
+            const uint32_t j = ent & kIndexMask;
             const float4 wi = w.vi[owner];
-            const float4 vj = __ldg(vel + __float_as_uint(q.w));
+            const float4 vj = __ldg(vel + j);
             const float dx = q.x, dy = q.y, dz = q.z;
             const float d2 = dist2_rn(dx, dy, dz);
             const float inv_r = rsqrtf(d2);
@@ -306,7 +308,7 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             uint32_t A, B;
             pair_hash(__float_as_uint(wi.w), __float_as_uint(vj.w), key, A, B);
             const float xi = gauss_from_hash(A, B);
-            const float a = ONE_SPECIES ? P.a[0] : a_tab[__float_as_int(w.pi[owner].w) * P.n_species + (int)(qo >> 5)];
+            const float a = ONE_SPECIES ? P.a[0] : a_tab[__float_as_int(w.pi[owner].w) * P.n_species + (int)qo];
             const float F = fmaf(a, wgt, fmaf(-P.gamma * wR * wR, ev, P.sigma_isdt * wR * xi));
             // conservative virial r_ij . F^C_ij (each pair once in Newton-3
             // mode, from both ends otherwise)
@@ -316,7 +318,7 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
             fy = sc * dy;
             fz = sc * dz;
             // Newton's third law: the partner gets -F once
-            if (N3) red_add_f4(facc + __float_as_uint(q.w), -fx, -fy, -fz);
+            if (N3) red_add_f4(facc + j, -fx, -fy, -fz);
         }
         // Per-owner sums: the queue follows the list, whose entries come
         // owner by owner, so a batch holds a few runs of equal owners.  A
@@ -378,8 +380,9 @@ __device__ __forceinline__ void warp_pairs(const SimParams &P, const float4 *__r
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, hit);
         if (hit) {
             const uint32_t slot = (tail + (uint32_t)__popc(m & lt_mask)) & (kQueue - 1);
-            w.q[slot] = make_float4(d.x, d.y, d.z, __uint_as_float(e & kIndexMask));
-            w.qo[slot] = (uint8_t)(own | (ONE_SPECIES ? 0u : ((uint32_t)__float_as_int(pj.w) << 5)));
+            // the entry keeps its owner bits; one species needs nothing else
+            w.q[slot] = make_float4(d.x, d.y, d.z, __uint_as_float(e));
+            if (!ONE_SPECIES) w.qo[slot] = (uint8_t)((uint32_t)__float_as_int(pj.w));
         }
         tail += (uint32_t)__popc(m);
         __syncwarp();
