@@ -115,7 +115,9 @@ struct Ptrs {
     float4 *pos[2], *vel[2], *vkick[2], *force[2];
     uint32_t *tag[2], *pid[2];
     float4 *xref;             // positions at the last rebuild
-    float4 *facc;             // Newton-3 mode: the force of each particle, summed by vector reductions
+    float4 *facc[2];          // Newton-3 mode: the force of each particle, summed by vector reductions;
+                              // buffer (step & 1) takes step `step`'s sums while the pair kernel
+                              // clears the other one for the next step
     float4 *fout;             // output of a standalone force evaluation
     DevCtl *ctl;
     // cells

@@ -511,7 +511,8 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     }
     A((void **)&D.xref, f4);
     A((void **)&D.fout, f4);
-    A((void **)&D.facc, f4);
+    A((void **)&D.facc[0], f4);
+    A((void **)&D.facc[1], f4);
     A((void **)&D.key, u4);
     A((void **)&D.slot, u4);
     A((void **)&D.tmp_idx, u4);
@@ -533,7 +534,7 @@ dpd_status alloc_particles(dpd_sim *h, int64_t n, int cap)
     // partials of a pair kernel launched with fewer blocks than the largest count stay zero
     CUDA_TRY(h, cudaMemsetAsync(D.vir_part, 0, sizeof(double) * (size_t)((h->P.ngroups + kForceWarps - 1) / kForceWarps),
                                 h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(D.facc, 0, f4, h->stream));
+    for (int b = 0; b < 2; ++b) CUDA_TRY(h, cudaMemsetAsync(D.facc[b], 0, f4, h->stream));
     h->P.cap = cap;
     h->P.gcap = kGroup * cap;
     h->cap_alloc_n = n;
@@ -850,7 +851,7 @@ dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v
     CUDA_TRY(h, cudaMemsetAsync(D.force[0], 0, sizeof(float4) * n, h->stream));
     if (!h->P.lambda_half) CUDA_TRY(h, cudaMemsetAsync(D.vkick[0], 0, sizeof(float4) * n, h->stream));
     CUDA_TRY(h, cudaMemsetAsync((void *)D.bond_partner, 0xFF, sizeof(uint32_t) * (size_t)n * kMaxBonds, h->stream));
-    CUDA_TRY(h, cudaMemsetAsync(D.facc, 0, sizeof(float4) * n, h->stream));
+    for (int b = 0; b < 2; ++b) CUDA_TRY(h, cudaMemsetAsync(D.facc[b], 0, sizeof(float4) * n, h->stream));
     DevCtl c;
     std::memset(&c, 0, sizeof(c));
     c.step = step;

@@ -485,10 +485,14 @@ __global__ void __launch_bounds__(kForceThreads, kForceMinBlocks) k_force(SimPar
     const uint32_t *__restrict__ list = D.nbr + (size_t)gid * P.gcap;
     float vir = 0.0f;
     bool bad = false;
+    // Newton-3 sums of this step go to facc[step & 1]; the other buffer,
+    // read by the previous step's settle kernel, is cleared here for the next
+    float4 *facc = D.facc[(uint32_t)step0 & 1u];
+    if (N3 && valid) D.facc[((uint32_t)step0 & 1u) ^ 1u][i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (all_interior)
-        warp_pairs<ONE_SPECIES, SMODE, false, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir, owners, bad);
+        warp_pairs<ONE_SPECIES, SMODE, false, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, facc, vir, owners, bad);
     else
-        warp_pairs<ONE_SPECIES, SMODE, true, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, D.facc, vir, owners, bad);
+        warp_pairs<ONE_SPECIES, SMODE, true, N3, VIR>(P, pos, vel, list, nent, lane, w, a_tab, facc, vir, owners, bad);
     if (kChecked && __any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(&ctl->err, kErrBadIndex);
     float fx = w.acc[0][lane], fy = w.acc[1][lane], fz = w.acc[2][lane];
 
@@ -497,7 +501,7 @@ __global__ void __launch_bounds__(kForceThreads, kForceMinBlocks) k_force(SimPar
         // groups pushed into facc; the settle kernel completes the mode
         if (valid) {
             add_bonds_body(P, D, i, pi, pos, opar, fx, fy, fz, VIR ? &vir : nullptr);
-            red_add_f4(D.facc + i, fx, fy, fz);
+            red_add_f4(facc + i, fx, fy, fz);
         }
         if (VIR) block_sum_double(vir, D.vir_part + blockIdx.x);
         return;
@@ -603,10 +607,11 @@ __global__ void __launch_bounds__(kForceThreads) k_force_rows(SimParams P, Ptrs 
     if (MODE != kForceEval) finish_block(ctl, moved);
 }
 
-// Newton-3 mode: f_i = facc[i], the sum of the particle's own-group share and
-// the partner shares the pair kernel's reductions added, then the force
-// mode's final stage (store, or integrate into the other set).  Clears facc
-// for the next evaluation.
+// Newton-3 mode: f_i = facc[step & 1][i], the sum of the particle's own-group
+// share and the partner shares the pair kernel's reductions added, then the
+// force mode's final stage (store, or integrate into the other set).  A step
+// leaves the buffer to the next step's pair kernel, which clears it; a plain
+// evaluation (the step does not advance) clears it here.
 template <int MODE, bool LHALF>
 __global__ void __launch_bounds__(kThreads) k_settle(SimParams P, Ptrs D, int out_fout)
 {
@@ -615,12 +620,13 @@ __global__ void __launch_bounds__(kThreads) k_settle(SimParams P, Ptrs D, int ou
     const uint32_t opar = ctl->oparity;
     const unsigned long long step0 = ctl->step;
     bool moved = false;
+    float4 *facc = D.facc[(uint32_t)step0 & 1u];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-        const float4 f = D.facc[i];
+        const float4 f = facc[i];
         const float4 pi = D.pos[par][i];
         const float4 vi = D.vel[par][i];
         moved |= integrate_particle<MODE, LHALF>(P, D, ctl, i, pi, vi, f.x, f.y, f.z, par, opar, step0, out_fout);
-        D.facc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MODE == kForceEval) facc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (MODE != kForceEval) finish_block(ctl, moved);
 }
