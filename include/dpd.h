@@ -246,6 +246,19 @@ dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *times);
 /* Observables of the current state. */
 dpd_status dpd_observables(dpd_sim *h, dpd_obs *out);
 
+/* The same observables, delivered asynchronously: the reduction is queued on
+ * the handle's stream behind the work already queued (e.g. dpd_step_async),
+ * so it describes the state that work reaches, and the finished dpd_obs is
+ * copied into *out.  out must be page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister or a pinned tensor) owned by the caller; its contents are
+ * valid after the next dpd_sync (or any call that waits on the handle), and
+ * bit-identical to what dpd_observables returns for the same state.  Returns
+ * DPD_ERR_ARG if out is NULL or not page-locked; errors of the queued work
+ * are reported by dpd_sync, and the values written then are not meaningful.
+ * Lets a run read its statistics every step (Alg. 1 "calculate
+ * statistics") without a host wait per step. */
+dpd_status dpd_observables_async(dpd_sim *h, dpd_obs *out);
+
 /* Binned profile of v[vel_axis] along bin_axis (nbins equal bins over the
  * box): sum_out[b] += sum of v, count_out[b] += number of particles.
  * Both arrays have nbins entries and are accumulated into, not cleared. */

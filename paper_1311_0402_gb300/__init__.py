@@ -29,6 +29,7 @@ EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds"
            "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled",
            "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error", "dpd_set_force",
            "dpd_step_async", "dpd_sync", "dpd_query", "dpd_tune_skin", "dpd_wait_selftest",
+           "dpd_observables_async",
            # include/dpd_server.h
            "dpd_server_default_options", "dpd_server_create", "dpd_server_submit", "dpd_server_wait",
            "dpd_server_now", "dpd_server_counts", "dpd_server_last_error", "dpd_server_destroy",
@@ -211,6 +212,7 @@ def lib():
         L.dpd_set_force.argtypes = [vp, P(f64)]
         L.dpd_step.argtypes = [vp, i64]
         L.dpd_observables.argtypes = [vp, P(dpd_obs)]
+        L.dpd_observables_async.argtypes = [vp, vp]
         L.dpd_step_profiled.argtypes = [vp, i64, P(dpd_step_times)]
         L.dpd_profile.argtypes = [vp, i32, i32, i32, P(f64), P(f64)]
         L.dpd_get_state.argtypes = [vp, P(f64), P(f64), P(u64)]
@@ -405,6 +407,35 @@ def dpd_observables(h) -> dict:
                 pressure=o.pressure, momentum=np.array(list(o.momentum)))
 
 
+def _obs_dict(o) -> dict:
+    return dict(step=o.step, n=o.n, kinetic=o.kinetic, temperature=o.temperature, virial=o.virial,
+                pressure=o.pressure, momentum=np.array(list(o.momentum)))
+
+
+def dpd_observables_async(h, address: int) -> None:
+    """Queue the observables into the page-locked dpd_obs at `address`
+    (valid after the next sync)."""
+    _check(lib().dpd_observables_async(h, ctypes.c_void_p(address)), h)
+
+
+class ObsBuffer:
+    """k dpd_obs records in page-locked host memory (a pinned torch tensor),
+    the destination of Sim.observables_async."""
+
+    def __init__(self, k: int):
+        import torch
+        self.k = int(k)
+        self._t = torch.zeros(self.k * ctypes.sizeof(dpd_obs), dtype=torch.uint8, pin_memory=True)
+
+    def address(self, i: int) -> int:
+        if not 0 <= i < self.k:
+            raise IndexError(i)
+        return self._t.data_ptr() + i * ctypes.sizeof(dpd_obs)
+
+    def get(self, i: int) -> dict:
+        return _obs_dict(dpd_obs.from_address(self.address(i)))
+
+
 def dpd_profile(h, bin_axis: int, vel_axis: int, nbins: int, sums=None, counts=None):
     s = np.zeros(nbins, np.float64) if sums is None else sums
     c = np.zeros(nbins, np.float64) if counts is None else counts
@@ -553,6 +584,11 @@ class Sim:
 
     def observables(self):
         return dpd_observables(self.h)
+
+    def observables_async(self, buf: "ObsBuffer", i: int):
+        """Queue the observables of the state the queued steps reach into
+        buf's record i; read it with buf.get(i) after sync()."""
+        dpd_observables_async(self.h, buf.address(i))
 
     def profile(self, bin_axis, vel_axis, nbins, sums=None, counts=None):
         return dpd_profile(self.h, bin_axis, vel_axis, nbins, sums, counts)

@@ -120,6 +120,7 @@ struct Ptrs {
                               // clears the other one for the next step
     float4 *fout;             // output of a standalone force evaluation
     DevCtl *ctl;
+    unsigned long long *obs;  // the 9 words of a dpd_obs, written by k_obs_finish
     // cells
     const uint32_t *rank_of_cell;  // (cz * nc_y + cy) * nc_x + cx -> Morton rank
     const uint32_t *stencil;       // [ncell][27] neighbour ranks, ascending, kNone pad
@@ -180,6 +181,7 @@ cudaError_t launch_force(const SimParams &P, const Ptrs &D, int mode, bool out_f
 // observables: nblocks per-block partials in D.red, then their fixed-order
 // sum in D.red[nblocks * 8 .. + 8)
 cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaStream_t s);
+cudaError_t launch_observe_finish(const Ptrs &D, int nblocks, int64_t n, double dof, double three_v, cudaStream_t s);
 // state transfer in the caller's layout (kernels_io.cu): validation of FP64
 // x, v and species (bits into *bad), conversion into the device layout, and
 // the scatter of a float4 array to FP64 triples in caller order

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -747,6 +748,7 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
     dpd_status st = DPD_OK;
     auto A = [&](void **p, size_t b) { if (st == DPD_OK) st = dev_alloc(h, p, b, h->static_allocs); };
     A((void **)&h->D.ctl, sizeof(DevCtl));
+    A((void **)&h->D.obs, sizeof(dpd_obs));
     A((void **)&h->D.rank_of_cell, sizeof(uint32_t) * P.ncell);
     A((void **)&h->D.stencil, sizeof(uint32_t) * (size_t)P.ncell * kStencil);
     A((void **)&h->D.cell_count, sizeof(uint32_t) * P.ncell);
@@ -1195,6 +1197,31 @@ dpd_status dpd_observables(dpd_sim *h, dpd_obs *out)
     out->momentum[0] = acc[1];
     out->momentum[1] = acc[2];
     out->momentum[2] = acc[3];
+    return DPD_OK;
+}
+
+static_assert(sizeof(dpd_obs) == 9 * 8 && offsetof(dpd_obs, step) == 0 && offsetof(dpd_obs, n) == 8 &&
+                  offsetof(dpd_obs, kinetic) == 16 && offsetof(dpd_obs, temperature) == 24 &&
+                  offsetof(dpd_obs, virial) == 32 && offsetof(dpd_obs, pressure) == 40 &&
+                  offsetof(dpd_obs, momentum) == 48,
+              "k_obs_finish writes dpd_obs as nine 8-byte words");
+
+dpd_status dpd_observables_async(dpd_sim *h, dpd_obs *out)
+{
+    NvtxRange nvtx_("dpd_observables_async");
+    dpd_status st = guard(h, true);
+    if (st) return st;
+    if (!out) return fail(h, DPD_ERR_ARG, "out is NULL");
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return fail(h, DPD_ERR_ARG, "out must be page-locked host memory");
+    }
+    const int nb = observe_blocks_for((int)h->n);
+    const double V = h->box[0] * h->box[1] * h->box[2];
+    CUDA_TRY(h, launch_observe(h->P, h->D, nb, h->stream));
+    CUDA_TRY(h, launch_observe_finish(h->D, nb, h->n, h->n > 1 ? 3.0 * h->n - 3.0 : 0.0, 3.0 * V, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(out, h->D.obs, sizeof(dpd_obs), cudaMemcpyDeviceToHost, h->stream));
     return DPD_OK;
 }
 

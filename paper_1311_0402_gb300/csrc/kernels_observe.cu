@@ -138,6 +138,24 @@ __global__ void k_pair_rng(uint64_t seed, uint32_t step, int64_t m, const uint32
     }
 }
 
+// One thread: the derived observables of the sums k_reduce8 left (v^2,
+// momentum, virial), by the same expressions as the host side of
+// dpd_observables with its divisors passed in (3N - 3 and 3V), stored as the
+// nine 8-byte words of a dpd_obs: step, n, kinetic, temperature, virial,
+// pressure, momentum[3].
+__global__ void k_obs_finish(const double *sums, const DevCtl *ctl, long long n, double dof, double three_v,
+                             unsigned long long *out)
+{
+    const double s0 = sums[0], vir = sums[4];
+    out[0] = ctl->step;
+    out[1] = (unsigned long long)n;
+    out[2] = (unsigned long long)__double_as_longlong(0.5 * s0);
+    out[3] = (unsigned long long)__double_as_longlong(dof > 0.0 ? s0 / dof : 0.0);
+    out[4] = (unsigned long long)__double_as_longlong(vir);
+    out[5] = (unsigned long long)__double_as_longlong((s0 + vir) / three_v);
+    for (int k = 0; k < 3; ++k) out[6 + k] = (unsigned long long)__double_as_longlong(sums[1 + k]);
+}
+
 }  // namespace
 
 int observe_blocks_for(int n)
@@ -150,6 +168,12 @@ cudaError_t launch_observe(const SimParams &P, const Ptrs &D, int nblocks, cudaS
 {
     k_observe<<<nblocks, kThreads, 0, s>>>(P, D);
     k_reduce8<<<1, kThreads, 0, s>>>(D.red, nblocks, D.red + (size_t)nblocks * 8);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe_finish(const Ptrs &D, int nblocks, int64_t n, double dof, double three_v, cudaStream_t s)
+{
+    k_obs_finish<<<1, 1, 0, s>>>(D.red + (size_t)nblocks * 8, D.ctl, (long long)n, dof, three_v, D.obs);
     return cudaGetLastError();
 }
 

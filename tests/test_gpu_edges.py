@@ -1,6 +1,8 @@
 """Edge cases of the GPU path: degenerate particle counts, a dense clump
 (neighbour capacity grows), particles on cell faces, argument and
 call-order errors, determinism, and checkpoint / resume."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -295,3 +297,45 @@ def test_force_overflow_during_a_step_latches_nonfinite(deterministic):
     g.step(2)
     assert np.all(np.isfinite(g.state()[0]))
     g.close()
+
+
+def test_async_observables_match_sync_every_step():
+    """dpd_observables_async queued behind single steps gives, once synced,
+    the same bits dpd_observables returns for each of those states (the same
+    run repeated with a host wait per step), with consecutive step numbers;
+    a destination that is not page-locked is refused."""
+    st = workloads.make("fluid_small")
+    c = st["cfg"]
+    k = 6
+
+    def run():
+        # deterministic mode: two runs of the same state are bit-identical
+        return dpd.Sim(c["box"], c["a"], c["gamma"], c["kT"], c["rc"], c["s"], c["dt"], seed=3, deterministic=1)
+
+    a = run()
+    a.set_state(st["x"], st["v"])
+    buf = dpd.ObsBuffer(k)
+    for i in range(k):
+        a.step_async(1)
+        a.observables_async(buf, i)
+    a.sync()
+    got = [buf.get(i) for i in range(k)]
+    b = run()
+    b.set_state(st["x"], st["v"])
+    want = []
+    for i in range(k):
+        b.step(1)
+        want.append(b.observables())
+    for g_, w_ in zip(got, want):
+        for key in ("step", "n", "kinetic", "temperature", "virial", "pressure"):
+            assert g_[key] == w_[key], (key, g_[key], w_[key])
+        assert np.array_equal(g_["momentum"], w_["momentum"])
+    assert [g_["step"] for g_ in got] == list(range(1, k + 1))
+    pageable = dpd.dpd_obs()
+    with pytest.raises(dpd.DPDError):
+        dpd.dpd_observables_async(a.h, ctypes.addressof(pageable))
+    # the refusal leaves the handle usable
+    a.step(1)
+    assert a.observables()["step"] == k + 1
+    a.close()
+    b.close()
