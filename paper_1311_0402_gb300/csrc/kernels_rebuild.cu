@@ -21,6 +21,8 @@
 //              compacted by warp ballots as in the paper's builder (Sec. 3.3);
 //              the list order depends only on the positions
 #include "dpd_internal.cuh"
+
+#include <type_traits>
 #include "dpd_math.cuh"
 #include "brick.cuh"
 
@@ -358,8 +360,15 @@ __global__ void k_nbuild(SimParams P, Ptrs D)
 // positions from global memory.
 constexpr int kBuildThreads = 256;
 constexpr int kBuildWarps = kBuildThreads / 32;
-constexpr int kSlots = 4;               // candidates per lane and chunk, held in registers
+constexpr int kSlots = 3;               // candidates per lane and chunk, held in registers
 constexpr int kChunk = 32 * kSlots;     // chunk of the candidate sequence
+// Three candidates per lane and four resident blocks per SM (64 registers,
+// no spill): 0.809 against 0.848 ms per rebuild on the 3M fluid with four
+// candidates and three blocks (80 registers).  A cell whose sequence needs a
+// second chunk interleaves its owners' entries chunk by chunk, which costs the
+// pair kernel 1 % (0.311 against 0.308 ms); two candidates per lane cost it
+// 2.5 % for a smaller builder gain.
+constexpr int kBuildMinBlocks = 4;
 
 template <bool WRAP>
 __device__ __forceinline__ bool within_list(const SimParams &P, float4 pj, float4 pi)
@@ -391,6 +400,21 @@ __device__ __forceinline__ float pair_d2(const SimParams &P, float4 pj, float4 p
         dz = __fsub_rn(pj.z, pi.z);
     }
     return dist2_rn(dx, dy, dz);
+}
+
+// fn(std::integral_constant<int, m>) with m = ns clamped to [1, M]: the pass
+// instantiated for the chunk's number of live slots (never more than the
+// candidate registers hold).
+template <int M, typename F>
+__device__ __forceinline__ void with_slots(uint32_t ns, F &&fn)
+{
+    if constexpr (M > 1) {
+        if (ns < (uint32_t)M) {
+            with_slots<M - 1>(ns, fn);
+            return;
+        }
+    }
+    fn(std::integral_constant<int, M>{});
 }
 
 // Per-warp table of one slot of the candidate sequence: head[l] is the
@@ -589,30 +613,23 @@ __device__ __forceinline__ uint32_t build_cell(const SimParams &P, const float4 
         const uint32_t ns = (c1 - c0 + 31u) / 32u;  // live slots of this chunk
         if (ROWS) {
             // list = the whole table, gcap = the row capacity
-            if (ns == 4u)
-                owner_pass_rows<WRAP, STAGED, 4>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
-            else if (ns == 3u)
-                owner_pass_rows<WRAP, STAGED, 3>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
-            else if (ns == 2u)
-                owner_pass_rows<WRAP, STAGED, 2>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
-            else
-                owner_pass_rows<WRAP, STAGED, 1>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, w.rows);
+            with_slots<kSlots>(ns, [&](auto m) {
+                owner_pass_rows<WRAP, STAGED, decltype(m)::value>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0,
+                                                                  c1, first, lane, list, gcap, w.rows);
+            });
             continue;
         }
-        if (ns == 4u)
-            total = owner_pass<WRAP, STAGED, HALF, 4, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
-        else if (ns == 3u)
-            total = owner_pass<WRAP, STAGED, HALF, 3, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
-        else if (ns == 2u)
-            total = owner_pass<WRAP, STAGED, HALF, 2, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
-        else
-            total = owner_pass<WRAP, STAGED, HALF, 1, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own, p_lo, p_hi, c0, c1, first, lane, list, gcap, total, &w.count);
+        with_slots<kSlots>(ns, [&](auto m) {
+            total = owner_pass<WRAP, STAGED, HALF, decltype(m)::value, ATOMIC>(P, pos, s_pos, s_off, cand, t, g_own,
+                                                                           p_lo, p_hi, c0, c1, first, lane, list, gcap,
+                                                                           total, &w.count);
+        });
     }
     return total;
 }
 
 template <bool ATOMIC, bool ROWS>
-__global__ void __launch_bounds__(kBuildThreads, 3) k_nbuild_brick(SimParams P, Ptrs D)
+__global__ void __launch_bounds__(kBuildThreads, kBuildMinBlocks) k_nbuild_brick(SimParams P, Ptrs D)
 {
     if (!D.ctl->rebuild) return;
     extern __shared__ float4 s_pos[];  // [P.brick_cap] staged halo positions
