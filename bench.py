@@ -622,6 +622,14 @@ def main():
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz (unit counts and max clock)"}
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (152 * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    # measured issue rates of the same lanes (FP32 FMA chains, integer xor+add
+    # chains), beside the nominal peak from unit counts and clock
+    ffma = dpd.dpd_alu_peak(0, 20)["lane_ops_per_s"] / 1e12
+    iop = dpd.dpd_alu_peak(1, 20)["lane_ops_per_s"] / 1e12
+    roofline["measured_issue"] = {"ffma": ffma, "int_xor_add": iop, "unit": "TOP/s",
+                                  "frac_of_measured_ffma": achieved / ffma,
+                                  "what": "dpd_alu_peak: 8 independent chains per thread, 8 blocks of 256 "
+                                          "threads per SM, 20 timed launches"}
     # the whole step against the same peak: the pair work plus the integrator's
     # lane-ops per particle, over the measured time per step (rebuilds included)
     step_ops = n * (pairs_per_particle * OPS_PER_PAIR + OPS_INTEGRATE)

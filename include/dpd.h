@@ -272,6 +272,18 @@ dpd_status dpd_get_state(dpd_sim *h, double *x, double *v, uint64_t *step);
 /* Number of particles and of neighbour-list rebuilds so far. */
 dpd_status dpd_info(dpd_sim *h, int64_t *n, int64_t *rebuilds, int32_t *nbr_capacity);
 
+/* Issue-rate probe for the denominator of the ALU roofline the pair kernel
+ * is measured against (152 SMs x 128 FP32/INT32 lanes x clock): kind 0 times
+ * chains of FP32 fused multiply-adds (one lane-op each), kind 1 chains of
+ * 32-bit integer xor-then-add (two lane-ops per link); every thread carries
+ * eight independent chains, eight blocks of 256 threads per SM.  One warm-up
+ * launch, then `reps` (1..1000) timed launches with CUDA events on a
+ * temporary stream of the current device.  *lane_ops_per_s receives the
+ * measured lane-operations per second, *ms_per_launch the mean launch time
+ * (either may not be NULL).  DPD_ERR_ARG for another kind or reps out of
+ * range, DPD_ERR_CUDA for a failed launch. */
+dpd_status dpd_alu_peak(int32_t kind, int32_t reps, double *lane_ops_per_s, double *ms_per_launch);
+
 /* The pair random numbers, computed by the device kernels (Sec. 3.5):
  * for each k, sig = TEA-16 signature of (bitrev(tag), step) under the key
  * of seed, (A, B) = TEA-4 of (min(sig_i, sig_j), max(sig_i, sig_j)),

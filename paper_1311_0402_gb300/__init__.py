@@ -29,7 +29,7 @@ EXPORTS = ("dpd_default_options", "dpd_create", "dpd_set_state", "dpd_set_bonds"
            "dpd_get_state", "dpd_info", "dpd_pair_rng", "dpd_last_error", "dpd_destroy", "dpd_step_profiled",
            "dpd_forces_static", "dpd_forces_static_max_particles", "dpd_forces_static_last_error", "dpd_set_force",
            "dpd_step_async", "dpd_sync", "dpd_query", "dpd_tune_skin", "dpd_wait_selftest",
-           "dpd_observables_async",
+           "dpd_observables_async", "dpd_alu_peak",
            # include/dpd_server.h
            "dpd_server_default_options", "dpd_server_create", "dpd_server_submit", "dpd_server_wait",
            "dpd_server_now", "dpd_server_counts", "dpd_server_last_error", "dpd_server_destroy",
@@ -213,6 +213,7 @@ def lib():
         L.dpd_step.argtypes = [vp, i64]
         L.dpd_observables.argtypes = [vp, P(dpd_obs)]
         L.dpd_observables_async.argtypes = [vp, vp]
+        L.dpd_alu_peak.argtypes = [i32, i32, P(f64), P(f64)]
         L.dpd_step_profiled.argtypes = [vp, i64, P(dpd_step_times)]
         L.dpd_profile.argtypes = [vp, i32, i32, i32, P(f64), P(f64)]
         L.dpd_get_state.argtypes = [vp, P(f64), P(f64), P(u64)]
@@ -410,6 +411,14 @@ def dpd_observables(h) -> dict:
 def _obs_dict(o) -> dict:
     return dict(step=o.step, n=o.n, kinetic=o.kinetic, temperature=o.temperature, virial=o.virial,
                 pressure=o.pressure, momentum=np.array(list(o.momentum)))
+
+
+def dpd_alu_peak(kind: int, reps: int = 20) -> dict:
+    """Measured issue rate of FP32 FMA (kind 0) or integer xor+add (kind 1)
+    chains, in lane-operations per second."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().dpd_alu_peak(int(kind), int(reps), ctypes.byref(r), ctypes.byref(ms)))
+    return {"lane_ops_per_s": r.value, "ms_per_launch": ms.value}
 
 
 def dpd_observables_async(h, address: int) -> None:

@@ -198,6 +198,7 @@ cudaError_t launch_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint3
 int scan_blocks_for(int ncell);
 // the bounded device wait on a transaction that never arrives (failure-detection probe)
 cudaError_t launch_wait_probe(const Ptrs &D, uint32_t polls, cudaStream_t s);
+cudaError_t time_alu_peak(int kind, int reps, double *lane_ops_per_s, double *ms_per_launch);
 // one-time kernel attributes (dynamic shared memory of the brick kernels)
 cudaError_t init_kernel_attributes();
 // largest brick_cap the builder's shared-memory limit allows

@@ -1321,6 +1321,18 @@ dpd_status dpd_pair_rng(uint64_t seed, uint64_t step, int64_t m, const uint32_t 
     return DPD_OK;
 }
 
+dpd_status dpd_alu_peak(int32_t kind, int32_t reps, double *lane_ops_per_s, double *ms_per_launch)
+{
+    if ((kind != 0 && kind != 1) || reps < 1 || reps > 1000 || !lane_ops_per_s || !ms_per_launch)
+        return fail(nullptr, DPD_ERR_ARG, "dpd_alu_peak: kind must be 0 or 1, reps 1..1000, outputs non-NULL");
+    const cudaError_t e = time_alu_peak(kind, reps, lane_ops_per_s, ms_per_launch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, DPD_ERR_CUDA, std::string("dpd_alu_peak: ") + cudaGetErrorString(e));
+    }
+    return DPD_OK;
+}
+
 const char *dpd_last_error(const dpd_sim *h)
 {
     if (h) return h->err.c_str();
