@@ -83,6 +83,11 @@ def test_argument_and_state_errors():
     x[1, 2] = np.nan
     with pytest.raises(dpd.DPDError):
         g.set_state(x, np.zeros((3, 3)))
+    # the particle count is checked before any array is read: one past the
+    # 2^27 a list entry can index is refused (the C call, small buffers)
+    buf = np.zeros((3, 3))
+    ptr = buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert dpd.lib().dpd_set_state(g.h, (1 << 27) + 1, ptr, ptr, None, None, 0) == 1  # DPD_ERR_ARG
     g.close()
 
 
