@@ -344,3 +344,26 @@ def test_async_observables_match_sync_every_step():
     assert a.observables()["step"] == k + 1
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("deterministic", [0, 1])
+def test_coincident_particles(deterministic):
+    """Pairs at r = 0 (60 particles moved onto others of the fluid): the list
+    keeps them (d^2 = 0 < r_list^2, as the oracle's FP32 brute force does), the
+    pair contributes no force on either side (e_ij is undefined there), every
+    other force matches the oracle, and steps stay finite."""
+    st = workloads.make("fluid_small")
+    x = st["x"].copy()
+    x[3000 - 60:] = x[:60]
+    g, o = make_pair(CFG, deterministic=deterministic)
+    g.set_state(x, st["v"], step=2)
+    x32, v32, _ = g.state()
+    assert np.array_equal(x32[3000 - 60:], x32[:60])
+    assert pair_set(g.neighbors()) == pair_set(oracle.pairs_fp32(x32, CFG["box"], 1.3))
+    fo, _ = o.forces(x32, v32, step=2)
+    err, _ = force_error(g.forces(), fo)
+    assert err < 1e-4, err
+    g.step(5)
+    xs, vs, _ = g.state()
+    assert np.isfinite(xs).all() and np.isfinite(vs).all()
+    g.close()
