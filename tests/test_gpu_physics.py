@@ -120,3 +120,60 @@ def test_reverse_poiseuille_full_size_start_up():
     assert abs(u[: nbins // 2].mean() + u[nbins // 2:].mean()) < 0.05 * abs(u).max()
     assert A > 0.03, A
     g.close()
+
+
+AMPH_BOX, AMPH_STEPS, AMPH_BURN, AMPH_EVERY = (10.0, 10.0, 10.0), 12000, 2000, 4
+
+
+def _oracle_amphiphile_means(seed):
+    """Time-averaged T and p of one oracle run of the small amphiphile box
+    (runs in a spawned worker process)."""
+    st = workloads.make("amphiphile", box=AMPH_BOX)
+    cfg = st["cfg"]
+    o = oracle.System(AMPH_BOX, cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"],
+                      lam=cfg.get("lam", 0.5), seed=seed, bonds=st["bonds"], k_bond=cfg["k_bond"],
+                      r0_bond=cfg["r0_bond"], cut_fp32=True)
+    x32 = st["x"].astype(np.float32).astype(np.float64)
+    res = o.run(x32, st["v"], AMPH_STEPS, species=st["species"])
+    obs = res["obs"][AMPH_BURN:]
+    T = oracle.System.temperature(obs[:, 0], st["n"]).mean()
+    p = o.pressure(obs[:, 0], obs[:, 1]).mean()
+    return float(T), float(p)
+
+
+def test_amphiphile_temperature_pressure_match_oracle():
+    """The bonded three-species amphiphile (H1T3 chains in W beads, a_WT =
+    a_HT = 75, harmonic bonds, dt = 0.005) in a 10^3 box: T and p averaged
+    over steps 2000-12000 agree within 1 %.  The chains self-assemble during
+    the run (p drifts by about 1.5 % across it), so one run's average varies
+    by about 0.3 % from seed to seed (measured on the oracle); the GPU side
+    averages eight seeds and the oracle two, which puts 1 % at about four
+    standard deviations of the difference."""
+    import multiprocessing as mp
+    st = workloads.make("amphiphile", box=AMPH_BOX)
+    cfg = st["cfg"]
+    n = st["n"]
+    with mp.get_context("spawn").Pool(2) as pool:
+        pending = pool.map_async(_oracle_amphiphile_means, [42, 7])
+        Tg, pg = [], []
+        for seed in range(101, 109):
+            g, _ = make_pair(cfg, box=AMPH_BOX, seed=seed)
+            g.set_state(st["x"], st["v"], st["species"])
+            g.set_bonds(st["bonds"], cfg["k_bond"], cfg["r0_bond"])
+            Ts, ps = [], []
+            for s in range(AMPH_STEPS // AMPH_EVERY):
+                g.step(AMPH_EVERY)
+                if (s + 1) * AMPH_EVERY > AMPH_BURN:
+                    ob = g.observables()
+                    Ts.append(ob["temperature"])
+                    ps.append(ob["pressure"])
+            g.close()
+            Tg.append(np.mean(Ts))
+            pg.append(np.mean(ps))
+        ref = pending.get(timeout=1800)
+    To = float(np.mean([r[0] for r in ref]))
+    po = float(np.mean([r[1] for r in ref]))
+    Tg, pg = float(np.mean(Tg)), float(np.mean(pg))
+    assert abs(Tg - To) < 0.01 * To, (Tg, To)
+    assert abs(pg - po) < 0.01 * po, (pg, po)
+    assert n == 3000
