@@ -1,9 +1,11 @@
 """Long-run physics: the GPU path and the FP64 oracle, each run on its own
 from the same FP32 initial state, must agree within 1 % in time-averaged
-temperature and pressure, and in the reverse-Poiseuille velocity profile
-(fitted amplitude within 2 %: the profile is a noisy mean of a chaotic
-trajectory; 2 % is five standard errors of the difference); the full-size
-reverse-Poiseuille run must follow the analytic parabola (Sec. 4.2)."""
+temperature and pressure (the fluid, and the bonded three-species
+amphiphile over several seeds a side), and in the reverse-Poiseuille velocity
+profile within four standard deviations of the difference of the two sides'
+seed means (the amplitude of a small box's profile varies by about 3 % from
+seed to seed); the full-size reverse-Poiseuille start-up must follow the
+analytic parabola (Sec. 4.2)."""
 import numpy as np
 import pytest
 
@@ -59,41 +61,61 @@ def _fit_amplitude(sums, counts, Ly, nbins):
     return A, r2
 
 
+POIS_BOX, POIS_NBINS, POIS_STEPS, POIS_BURN, POIS_EVERY = (16.0, 10.0, 5.0), 10, 7000, 2500, 5
+
+
+def _oracle_poiseuille_amplitude(seed):
+    """Fitted amplitude of one oracle run's time-averaged profile over steps
+    POIS_BURN..POIS_STEPS (runs in a spawned worker process)."""
+    st = workloads.make("poiseuille", box=POIS_BOX)
+    cfg = st["cfg"]
+    o = oracle.System(POIS_BOX, cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"],
+                      lam=cfg.get("lam", 0.5), seed=seed, body_mode=cfg.get("body_mode", 0),
+                      body=cfg.get("body", (0, 0, 0)), cut_fp32=True)
+    x32 = st["x"].astype(np.float32).astype(np.float64)
+    state = o.run(x32, st["v"], POIS_BURN)
+    state = o.run(state["x"], state["v"], POIS_STEPS - POIS_BURN, step=state["step"], f=state["f"],
+                  prof_nbins=POIS_NBINS, prof_from=1)
+    return _fit_amplitude(state["prof_sum"], state["prof_cnt"], POIS_BOX[1], POIS_NBINS)[0]
+
+
 def test_reverse_poiseuille_profile_matches_oracle():
     """16 x 10 x 5 box (rho = 4, s = 1/2, g = +-0.055): the amplitude of the
-    time-averaged double parabola, GPU (mean of 6 seeds) against the oracle
-    (one run).  The profile carries slow hydrodynamic noise, so the bound is
-    the larger of 1 % and three standard errors of the oracle's block means."""
-    box = (16.0, 10.0, 5.0)
-    nbins, nsteps, burn, every, block = 10, 7000, 2500, 5, 500
-    st = workloads.make("poiseuille", box=box)
+    double parabola averaged over steps 2500-7000, GPU (32 seeds) against the
+    oracle (16 seeds, in spawned worker processes).  One run's amplitude
+    varies by about 3 % from seed to seed (the profile of a box this small
+    carries slow hydrodynamic noise; eight oracle seeds: 0.0679 to 0.0734), so
+    a flat 1 % would need some 260 runs a side.  The bound is four standard
+    deviations of the difference of the two means, from each side's own
+    seed-to-seed spread (about 3.6 %), and it must itself stay below 6 %."""
+    import multiprocessing as mp
+    import os
+    st = workloads.make("poiseuille", box=POIS_BOX)
     cfg = st["cfg"]
-    amps = []
-    for seed in range(6):
-        g, o = make_pair(cfg, box=box, seed=42 + seed)
-        g.set_state(st["x"], st["v"])
-        if seed == 0:
-            x32, v32, _ = g.state()
-        sg, cg = np.zeros(nbins), np.zeros(nbins)
-        g.step(burn)
-        for s in range((nsteps - burn) // every):
-            g.step(every)
-            g.profile(1, 0, nbins, sg, cg)
-        amps.append(_fit_amplitude(sg, cg, box[1], nbins)[0])
-        g.close()
-    Ag = float(np.mean(amps))
-    _, o = make_pair(cfg, box=box, seed=42)
-    res = o.run(x32, v32, burn)
-    blocks = []
-    state = res
-    for b in range((nsteps - burn) // block):
-        state = o.run(state["x"], state["v"], block, step=state["step"], f=state["f"], prof_nbins=nbins, prof_from=1)
-        blocks.append(_fit_amplitude(state["prof_sum"], state["prof_cnt"], box[1], nbins)[0])
-    Ao = float(np.mean(blocks))
-    se = float(np.std(blocks, ddof=1) / np.sqrt(len(blocks)))
-    tol = max(0.01 * abs(Ao), 3.0 * se)
-    assert abs(Ag - Ao) < tol, (Ag, Ao, se)
-    r2 = _fit_amplitude(sg, cg, box[1], nbins)[1]
+    seeds_o = list(range(42, 58))
+    workers = max(1, min(len(seeds_o), os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        pending = pool.map_async(_oracle_poiseuille_amplitude, seeds_o)
+        amps, last = [], None
+        for seed in range(1000, 1032):
+            g, _ = make_pair(cfg, box=POIS_BOX, seed=seed)
+            g.set_state(st["x"], st["v"])
+            sg, cg = np.zeros(POIS_NBINS), np.zeros(POIS_NBINS)
+            g.step(POIS_BURN)
+            for s in range((POIS_STEPS - POIS_BURN) // POIS_EVERY):
+                g.step(POIS_EVERY)
+                g.profile(1, 0, POIS_NBINS, sg, cg)
+            amps.append(_fit_amplitude(sg, cg, POIS_BOX[1], POIS_NBINS)[0])
+            last = (sg, cg)
+            g.close()
+        ref = np.array(pending.get(timeout=1800))
+    amps = np.array(amps)
+    Ag, Ao = float(amps.mean()), float(ref.mean())
+    sd_diff = float(np.sqrt(amps.var(ddof=1) / len(amps) + ref.var(ddof=1) / len(ref)))
+    tol = 4.0 * sd_diff
+    assert tol < 0.06 * abs(Ao), (tol, Ao)
+    assert abs(Ag - Ao) < tol, (Ag, Ao, sd_diff)
+    r2 = _fit_amplitude(last[0], last[1], POIS_BOX[1], POIS_NBINS)[1]
     assert r2 > 0.97, r2
 
 
