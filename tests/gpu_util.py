@@ -40,20 +40,3 @@ def force_error(f_gpu, f_ref):
 def pair_set(p):
     p = np.asarray(p, np.uint64).reshape(-1, 2)
     return set((p[:, 0] << np.uint64(32) | p[:, 1]).tolist())
-
-
-def block_se(samples, nblocks=10):
-    """Standard error of the mean of a correlated time series, from the
-    scatter of nblocks consecutive block means (no method arithmetic)."""
-    a = np.asarray(samples, np.float64)
-    m = len(a) // nblocks
-    b = a[: m * nblocks].reshape(nblocks, m).mean(1)
-    return float(b.std(ddof=1) / np.sqrt(nblocks))
-
-
-def agree(a, b, floor):
-    """Two independent runs' time averages agree: their difference is within
-    the larger of `floor` and four standard errors of the difference."""
-    se = np.hypot(block_se(a), block_se(b))
-    d = abs(float(np.mean(a)) - float(np.mean(b)))
-    return d < max(floor, 4.0 * se), (d, se)

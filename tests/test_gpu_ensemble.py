@@ -14,7 +14,7 @@ import pytest
 import oracle
 import paper_1311_0402_gb300 as dpd
 import workloads
-from gpu_util import agree, force_error, need_gpu
+from gpu_util import force_error, need_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -131,33 +131,44 @@ def test_per_box_steps_and_ids():
     ens2.close()
 
 
+SEEDS = 8  # boxes (random-force seeds) per side of a long-run comparison
+
+
 def test_thermodynamics_match_the_engine():
     """rho = 3, a = 25, kT = 1 in an L = 10 box: temperature and pressure over
-    a long run, ensemble kernel vs the neighbour-list engine (independent
-    random streams, so statistical agreement)."""
+    a long run, eight boxes in one ensemble against eight runs of the
+    neighbour-list engine (independent random streams).  One run's average T
+    varies by about 0.35 % from seed to seed, so the means over eight a side
+    are compared within 1 % (about 5.7 standard deviations of their
+    difference)."""
     box, x, v = _fluid(10, 103)
     ens = dpd.Ensemble()
-    i = _add(ens, box, x, v)
-    sim = dpd.Sim(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, deterministic=1)
-    sim.set_state(x, v)
+    ids = [_add(ens, box, x, v, seed=42 + k) for k in range(SEEDS)]
     ens.step(500)
-    sim.step(500)
-    te, pe, ts, ps = [], [], [], []
+    te, pe = [], []
     for _ in range(200):
         ens.step(20)
-        sim.step(20)
         ens.sync()
-        a, b = ens.observables(i), sim.observables()
-        te.append(a["temperature"]); pe.append(a["pressure"])
-        ts.append(b["temperature"]); ps.append(b["pressure"])
-    assert abs(np.mean(te) - 1.0) < 0.03 and 22.5 < np.mean(pe) < 25.0
-    ok, why = agree(te, ts, 0.01)
-    assert ok, why
-    ok, why = agree(pe, ps, 0.01 * np.mean(ps))
-    assert ok, why
-    assert abs(ens.observables(i)["momentum"]).max() < 1e-2
+        obs = [ens.observables(i) for i in ids]
+        te.append(np.mean([o["temperature"] for o in obs]))
+        pe.append(np.mean([o["pressure"] for o in obs]))
+    assert max(abs(ens.observables(i)["momentum"]).max() for i in ids) < 1e-2
     ens.close()
-    sim.close()
+    ts, ps = [], []
+    for k in range(SEEDS):
+        sim = dpd.Sim(box, [[25.0]], 4.5, 1.0, 1.0, 1.0, 0.01, deterministic=1, seed=142 + k)
+        sim.set_state(x, v)
+        sim.step(500)
+        for _ in range(200):
+            sim.step(20)
+            b = sim.observables()
+            ts.append(b["temperature"])
+            ps.append(b["pressure"])
+        sim.close()
+    Te, Pe, Ts, Ps = np.mean(te), np.mean(pe), np.mean(ts), np.mean(ps)
+    assert abs(Te - 1.0) < 0.03 and 22.5 < Pe < 25.0
+    assert abs(Te - Ts) < 0.01 * Ts, (Te, Ts)
+    assert abs(Pe - Ps) < 0.01 * Ps, (Pe, Ps)
 
 
 def test_reverse_poiseuille_body_force():
@@ -316,9 +327,12 @@ def test_newton3_trajectory_and_thermodynamics():
     dx = xg - res["x"]
     dx -= np.asarray(box) * np.round(dx / np.asarray(box))
     assert np.abs(dx).max() < 1e-5 and np.abs(vg - res["v"]).max() < 1e-3
-    # long run against the deterministic mode (independent rounding, same physics)
+    # long run against the deterministic mode (independent rounding, same
+    # physics): eight boxes (seeds) a side, means compared within 1 %
+    ens.remove(i)
+    ids3 = [_add(ens, box, x, v, seed=42 + k) for k in range(SEEDS)]
     det = dpd.Ensemble()
-    j = _add(det, box, x, v, seed=43)
+    idsd = [_add(det, box, x, v, seed=142 + k) for k in range(SEEDS)]
     ens.step(500)
     det.step(500)
     t3, p3, td, pd = [], [], [], []
@@ -327,14 +341,13 @@ def test_newton3_trajectory_and_thermodynamics():
         det.step(20)
         ens.sync()
         det.sync()
-        a, b = ens.observables(i), det.observables(j)
-        t3.append(a["temperature"]); p3.append(a["pressure"])
-        td.append(b["temperature"]); pd.append(b["pressure"])
-    ok, why = agree(t3, td, 0.01)
-    assert ok, why
-    ok, why = agree(p3, pd, 0.01 * np.mean(pd))
-    assert ok, why
-    assert abs(ens.observables(i)["momentum"]).max() < 1e-2
+        a = [ens.observables(k) for k in ids3]
+        b = [det.observables(k) for k in idsd]
+        t3.append(np.mean([o["temperature"] for o in a])); p3.append(np.mean([o["pressure"] for o in a]))
+        td.append(np.mean([o["temperature"] for o in b])); pd.append(np.mean([o["pressure"] for o in b]))
+    assert abs(np.mean(t3) - np.mean(td)) < 0.01 * np.mean(td), (np.mean(t3), np.mean(td))
+    assert abs(np.mean(p3) - np.mean(pd)) < 0.01 * np.mean(pd), (np.mean(p3), np.mean(pd))
+    assert max(abs(ens.observables(k)["momentum"]).max() for k in ids3) < 1e-2
     ens.close()
     det.close()
 

@@ -22,25 +22,50 @@ def _gpu():
     need_gpu()
 
 
-def test_fluid_temperature_pressure_match_oracle():
+FLUID_STEPS, FLUID_BURN, FLUID_EVERY = 4000, 800, 4
+
+
+def _oracle_fluid_means(seed):
+    """Time-averaged T and p of one oracle run of the 3000-particle fluid
+    (runs in a spawned worker process)."""
     st = workloads.make("fluid_small")
     cfg = st["cfg"]
-    n = st["n"]
-    g, o = make_pair(cfg)
-    g.set_state(st["x"], st["v"])
-    x32, v32, _ = g.state()
-    nsteps, burn, every = 4000, 800, 4
-    Tg, pg = [], []
-    for s in range(nsteps // every):
-        g.step(every)
-        if (s + 1) * every > burn:
-            ob = g.observables()
-            Tg.append(ob["temperature"])
-            pg.append(ob["pressure"])
-    res = o.run(x32, v32, nsteps)
-    obs = res["obs"][burn:]
-    To = oracle.System.temperature(obs[:, 0], n).mean()
-    po = o.pressure(obs[:, 0], obs[:, 1]).mean()
+    o = oracle.System(cfg["box"], cfg["a"], cfg["gamma"], cfg["kT"], cfg["rc"], cfg["s"], cfg["dt"], seed=seed,
+                      cut_fp32=True)
+    x32 = st["x"].astype(np.float32).astype(np.float64)
+    obs = o.run(x32, st["v"], FLUID_STEPS)["obs"][FLUID_BURN:]
+    return (float(oracle.System.temperature(obs[:, 0], st["n"]).mean()),
+            float(o.pressure(obs[:, 0], obs[:, 1]).mean()))
+
+
+def test_fluid_temperature_pressure_match_oracle():
+    """The 3000-particle fluid: T and p averaged over steps 800-4000 agree
+    within 1 %.  One run's average T varies by about 0.35 % from seed to seed
+    (p by 0.04 %; eight oracle seeds), so the GPU side averages eight seeds
+    and the oracle four (in spawned worker processes): 1 % is then about
+    4.7 standard deviations of the difference."""
+    import multiprocessing as mp
+    st = workloads.make("fluid_small")
+    cfg = st["cfg"]
+    with mp.get_context("spawn").Pool(4) as pool:
+        pending = pool.map_async(_oracle_fluid_means, [42, 43, 44, 45])
+        Tg, pg = [], []
+        for seed in range(201, 209):
+            g, _ = make_pair(cfg, seed=seed)
+            g.set_state(st["x"], st["v"])
+            Ts, ps = [], []
+            for s in range(FLUID_STEPS // FLUID_EVERY):
+                g.step(FLUID_EVERY)
+                if (s + 1) * FLUID_EVERY > FLUID_BURN:
+                    ob = g.observables()
+                    Ts.append(ob["temperature"])
+                    ps.append(ob["pressure"])
+            g.close()
+            Tg.append(np.mean(Ts))
+            pg.append(np.mean(ps))
+        ref = pending.get(timeout=1800)
+    To = float(np.mean([r[0] for r in ref]))
+    po = float(np.mean([r[1] for r in ref]))
     Tg, pg = float(np.mean(Tg)), float(np.mean(pg))
     assert abs(Tg - To) < 0.01 * To, (Tg, To)
     assert abs(pg - po) < 0.01 * po, (pg, po)
