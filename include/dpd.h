@@ -153,10 +153,14 @@ dpd_status dpd_set_bonds(dpd_sim *h, int64_t nb, const uint32_t *pairs, double k
  * if d < -L/2), d^2 = (dx dx + dy dy) + dz dz, each operation rounded. */
 dpd_status dpd_build_neighbors(dpd_sim *h);
 
-/* Copy the neighbour pairs of the current list as particle indices
- * (i < j), at most cap pairs into pairs_out (cap x 2), and the number of
- * distinct pairs into *n_out (which may exceed cap).  pairs_out may be
- * NULL with cap = 0 to query the count. */
+/* The cutoff neighbour list of Sec. 3.3 (every pair with d^2 < r_list^2,
+ * r_list = r_c + skin, by the predicate above, as of the last build): copy
+ * its pairs as caller particle indices (i < j, each pair once whatever the
+ * force mode), at most cap pairs into pairs_out (cap x 2 uint32, owned by the
+ * caller), and the number of distinct pairs into *n_out (which may exceed
+ * cap).  pairs_out may be NULL with cap = 0 to query the count.  Waits for
+ * the queued work.  DPD_ERR_STATE without a loaded state; DPD_ERR_ARG for
+ * cap < 0, pairs_out NULL with cap > 0, or n_out NULL. */
 dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64_t *n_out);
 
 /* Total force f_i = sum_j F_ij (Eq. 2) + bonds + body force at the current
@@ -166,7 +170,10 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
  * skin/2 since it was built). */
 dpd_status dpd_forces(dpd_sim *h, double *f_out);
 
-/* The force the integrator holds for the next step (n x 3). */
+/* The force the integrator holds for the next step (n x 3 doubles in the
+ * caller's order, owned by the caller): the pair force of Eqs. 2-9 plus bonds
+ * and the body force at the current positions, the f of Algorithm 1's next
+ * half kick.  Waits.  DPD_ERR_STATE without a state; DPD_ERR_ARG for NULL. */
 dpd_status dpd_get_force(dpd_sim *h, double *f_out);
 
 /* Replace the force the integrator holds (n x 3, caller's order, rounded to
@@ -243,7 +250,12 @@ typedef struct {
  * NULL. */
 dpd_status dpd_step_profiled(dpd_sim *h, int64_t nsteps, dpd_step_times *times);
 
-/* Observables of the current state. */
+/* Observables of the current full-step state (Algorithm 1's "calculate
+ * statistics"): T = sum m v^2 / (3N - 3), p = (sum m v^2 + virial) / (3V)
+ * with the virial of the conservative force (Eq. 3) and the bonds, kinetic
+ * energy and momentum, reduced on the device in a fixed order and summed in
+ * FP64.  *out is the caller's.  Waits for the queued work.  DPD_ERR_STATE
+ * without a state; DPD_ERR_ARG for NULL. */
 dpd_status dpd_observables(dpd_sim *h, dpd_obs *out);
 
 /* The same observables, delivered asynchronously: the reduction is queued on
@@ -259,14 +271,20 @@ dpd_status dpd_observables(dpd_sim *h, dpd_obs *out);
  * statistics") without a host wait per step. */
 dpd_status dpd_observables_async(dpd_sim *h, dpd_obs *out);
 
-/* Binned profile of v[vel_axis] along bin_axis (nbins equal bins over the
- * box): sum_out[b] += sum of v, count_out[b] += number of particles.
- * Both arrays have nbins entries and are accumulated into, not cleared. */
+/* Binned velocity profile, as the flow validations of Sec. 4.2 measure it:
+ * v[vel_axis] along bin_axis in nbins equal bins over the box,
+ * sum_out[b] += sum of v, count_out[b] += number of particles.  Both arrays
+ * (nbins doubles each, the caller's) are accumulated into, not cleared.
+ * Waits.  DPD_ERR_ARG for an axis outside 0..2, nbins outside 1..100000 or a
+ * NULL array; DPD_ERR_STATE without a state. */
 dpd_status dpd_profile(dpd_sim *h, int32_t bin_axis, int32_t vel_axis, int32_t nbins,
                        double *sum_out, double *count_out);
 
-/* Current state in the caller's particle order: x, v (n x 3, nullable) as
- * stored on the device (FP32 values, wrapped into [0, L)), and the step. */
+/* The integrator's state at the current full step (Sec. 3.1, Algorithm 1) in
+ * the caller's particle order: x, v (n x 3 doubles, owned by the caller, each
+ * nullable) as stored on the device (FP32 values, x wrapped into [0, L)), and
+ * the step (nullable).  Waits for the queued work.  DPD_ERR_STATE without a
+ * state. */
 dpd_status dpd_get_state(dpd_sim *h, double *x, double *v, uint64_t *step);
 
 /* Number of particles and of neighbour-list rebuilds so far. */
