@@ -137,20 +137,30 @@ dpd_status dpd_create(dpd_sim **out, const double box[3], int32_t n_species, con
  * random force, or NULL (tag = particle index).  step: the step number of
  * this state (keys the random force).  Builds the cell and neighbour lists
  * and computes the force at this state.  Replaces any previous state and
- * drops previously set bonds. */
+ * drops previously set bonds.  The arrays are the caller's and are copied.
+ * DPD_ERR_ARG for n outside that range, x or v NULL, a non-finite value, a
+ * species out of range or repeated tags; DPD_ERR_OOM when device memory runs
+ * out.  On any error the previous state (if any) is kept and stays usable. */
 dpd_status dpd_set_state(dpd_sim *h, int64_t n, const double *x, const double *v,
                          const int32_t *species, const uint32_t *tag, uint64_t step);
 
 /* Harmonic bonds F = -K (r - r0) e_ij between particle indices (Sec. 4.5).
  * pairs: nb x 2 particle indices (the order of dpd_set_state); each particle
  * may appear in at most 6 bonds.  Bonded pairs also feel the pair force.
- * Recomputes the force of the current state.  nb = 0 removes all bonds. */
+ * Recomputes the force of the current state.  nb = 0 removes all bonds.
+ * pairs is the caller's and is copied.  DPD_ERR_STATE without a state;
+ * DPD_ERR_ARG for nb < 0, a NULL pairs with nb > 0, a non-finite k or r0, an
+ * index out of range, a bond of a particle with itself or a seventh bond on a
+ * particle. */
 dpd_status dpd_set_bonds(dpd_sim *h, int64_t nb, const uint32_t *pairs, double k, double r0);
 
 /* Rebuild the cell list, particle order and neighbour list now (Secs. 3.2-3.3).
  * The list holds every pair with d^2 < (rc + skin)^2 under the FP32
  * minimum-image predicate d = x_j - x_i (per axis: d -= L if d > L/2, d += L
- * if d < -L/2), d^2 = (dx dx + dy dy) + dz dz, each operation rounded. */
+ * if d < -L/2), d^2 = (dx dx + dy dy) + dz dz, each operation rounded.  With
+ * automatic capacity the list grows when it overflows; with a fixed
+ * nbr_capacity an overflow returns DPD_ERR_NBR_OVERFLOW.  DPD_ERR_STATE
+ * without a state. */
 dpd_status dpd_build_neighbors(dpd_sim *h);
 
 /* The cutoff neighbour list of Sec. 3.3 (every pair with d^2 < r_list^2,
@@ -167,7 +177,8 @@ dpd_status dpd_get_neighbors(dpd_sim *h, int64_t cap, uint32_t *pairs_out, int64
  * positions, velocities and step key, into f_out (n x 3, nullable).  Does
  * not change the state.  Uses the current neighbour list, which every call
  * leaves valid for the current positions (no particle has moved more than
- * skin/2 since it was built). */
+ * skin/2 since it was built).  f_out is the caller's.  Waits.  DPD_ERR_STATE
+ * without a state; DPD_ERR_NONFINITE if a force is not finite. */
 dpd_status dpd_forces(dpd_sim *h, double *f_out);
 
 /* The force the integrator holds for the next step (n x 3 doubles in the
@@ -180,7 +191,8 @@ dpd_status dpd_get_force(dpd_sim *h, double *f_out);
  * FP32).  With dpd_get_state and dpd_get_force it completes a checkpoint:
  * the force held between steps was evaluated with the predicted velocity
  * v~ of the lambda scheme (Sec. 3.1), which dpd_set_state cannot recompute
- * from (x, v) alone. */
+ * from (x, v) alone.  f is the caller's and is copied.  DPD_ERR_STATE without
+ * a state; DPD_ERR_ARG for NULL or a non-finite value. */
 dpd_status dpd_set_force(dpd_sim *h, const double *f);
 
 /* Advance nsteps steps (Alg. 1 main loop, Sec. 3.1): for each step
@@ -287,7 +299,10 @@ dpd_status dpd_profile(dpd_sim *h, int32_t bin_axis, int32_t vel_axis, int32_t n
  * state. */
 dpd_status dpd_get_state(dpd_sim *h, double *x, double *v, uint64_t *step);
 
-/* Number of particles and of neighbour-list rebuilds so far. */
+/* Number of particles, of neighbour-list rebuilds so far (the rebuild branch
+ * of Algorithm 1) and the list capacity per particle; each output nullable.
+ * Waits for the queued work; without a state n, rebuilds and the capacity
+ * read 0. */
 dpd_status dpd_info(dpd_sim *h, int64_t *n, int64_t *rebuilds, int32_t *nbr_capacity);
 
 /* Issue-rate probe for the denominator of the ALU roofline the pair kernel
